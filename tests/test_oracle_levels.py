@@ -1,0 +1,85 @@
+"""Pins of one oracle level: Schur-complement null spaces, the coarse basis
+(eq. local_saddle_point_problem: C Psi = I, Psi^T S Psi = -mu, Sec. 5), the
+averaging operator E (eq. E-onto-U: E U = U, E^2 = E) and the box-vertex
+corner counts of the paper's 2x2x2 decomposition (12 faces, Table 1)."""
+import numpy as np
+import pytest
+
+import amb_inputs as ai
+from oracle import levels as lv
+
+
+def _level(prob, initial="ce"):
+    lev = lv.level_one(prob, initial)
+    lev.schur()
+    lev.coarse_basis()
+    return lev
+
+
+def _rigid_modes(lev, sb, prob):
+    nodes = lev.node_of_dof[sb.gdofs]
+    comp = lev.comp_of_dof[sb.gdofs]
+    nx1, ny1 = prob.nx + 1, prob.ny + 1
+    xyz = np.stack([nodes % nx1, (nodes // nx1) % ny1, nodes // (nx1 * ny1)], 1).astype(float)
+    modes = []
+    for c in range(3):
+        modes.append((comp == c).astype(float))
+    for ax in range(3):
+        r = np.cross(np.eye(3)[ax], xyz)
+        modes.append(r[np.arange(comp.size), comp])
+    return np.array(modes).T
+
+
+def test_floating_schur_null_space():
+    prob = ai.toy(4, 1, 11)
+    lev = _level(prob)
+    s1 = lev.subs[1].s        # sub 1 does not touch x = 0: floating
+    assert np.abs(s1 @ np.ones(s1.shape[0])).max() < 1e-10 * np.abs(s1).max()
+    prob3 = ai.toy(4, 3, 11)
+    lev3 = _level(prob3)
+    sb = lev3.subs[1]
+    r = _rigid_modes(lev3, sb, prob3)
+    assert np.abs(sb.s @ r).max() < 1e-9 * np.abs(sb.s).max()
+    # sub 0 is held by the Dirichlet face: its S is positive definite
+    assert np.linalg.eigvalsh(lev3.subs[0].s).min() > 0
+
+
+@pytest.mark.parametrize("dpn", [1, 3])
+def test_coarse_basis_identities(dpn):
+    prob = ai.toy(4, dpn, 5, split=(2, 2, 1))
+    lev = _level(prob)
+    for sb in lev.subs:
+        nc = sb.c.shape[0]
+        assert np.allclose(sb.c @ sb.psi, np.eye(nc), atol=1e-10)
+        assert np.allclose(sb.psi.T @ sb.s @ sb.psi, -sb.mu, atol=1e-9 * np.abs(sb.mu).max())
+    ac = lev.coarse_matrix()
+    assert np.linalg.eigvalsh(ac).min() > 0
+
+
+def test_averaging_is_projection_onto_U():
+    prob = ai.toy(4, 3, 2, split=(2, 2, 1))
+    lev = _level(prob)
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(lev.n)
+    ru = [u[sb.dofs] for sb in lev.subs]
+    assert np.allclose(lev.average(ru), u, atol=1e-13)          # E U = U (partition of unity)
+    z = [rng.standard_normal(sb.dofs.size) for sb in lev.subs]
+    ez = lev.average(z)
+    assert np.allclose(lev.average([ez[sb.dofs] for sb in lev.subs]), ez, atol=1e-13)  # E^2 = E
+    # weights sum to one on every interface dof
+    acc = np.zeros(lev.n)
+    for sb in lev.subs:
+        np.add.at(acc, sb.gdofs, sb.w)
+    iface = np.unique(np.concatenate([sb.gdofs for sb in lev.subs]))
+    assert np.allclose(acc[iface], 1.0, atol=1e-14)
+
+
+def test_classification_counts_2x2x2():
+    prob = ai.config(1)
+    lev = lv.level_one(prob)
+    # 3x3x3 box vertices, minus the 9 Dirichlet ones on x = 0, minus the 4 owned by one substructure
+    assert int(lev.node_corner.sum()) == 14
+    assert len(lev.edges) == 6
+    assert len(lev.faces) == 12
+    # every edge is shared by 4 substructures, every face by 2
+    assert all(len(k) == 4 for k in lev.edges)
