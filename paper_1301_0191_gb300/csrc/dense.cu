@@ -1,0 +1,537 @@
+// Batched dense kernels of the substructure engine: variable-size batched
+// GEMM (with triangular operands and lower-only output), batched GEMV,
+// blocked right-looking partial Cholesky and recursive-doubling triangular
+// inverse.  These carry the factorizations of Sec. 2 / Sec. 5 (A_II = L L^T,
+// S = K_GG - X^T X with X = L^{-1} K_IG, and the corner-constrained Neumann
+// factor S_DD = L_D L_D^T) and every solve with those factors.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "common.h"
+
+namespace amb {
+
+thread_local int64_t g_launches = 0;
+
+// ------------------------------------------------------------------ GEMM
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec2<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T>
+struct GemmArgs {
+  const GemmDesc* desc;
+  const int* prefix;   // ndesc+1 tile prefix sums
+  int ndesc;
+  int flags;
+  T alpha, beta;
+  const T* A;
+  const T* B;
+  T* C;
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm(GemmArgs<T> g) {
+  constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
+  constexpr int PAD = 16 / sizeof(T);
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
+  static_assert(LA * NT == BM * BK && LB * NT == BK * BN, "tile/thread mismatch");
+  __shared__ __align__(16) T As[2][BK][BM + PAD];
+  __shared__ __align__(16) T Bs[2][BK][BN + PAD];
+
+  const int bid = blockIdx.x;
+  int lo = 0, hi = g.ndesc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.prefix[mid] <= bid) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc d = g.desc[lo];
+  const int t = bid - g.prefix[lo];
+  const int tn = (d.n + BN - 1) / BN;
+  const int i0 = (t / tn) * BM, j0 = (t % tn) * BN;
+  const int fl = g.flags;
+  if ((fl & G_OUT_LOWER) && j0 > i0 + BM - 1) return;
+
+  int kbeg = 0, kend = d.k;
+  if (fl & G_TRI_A_LOWER) kend = min(kend, i0 + BM);
+  if (fl & G_TRI_B_UPPER) kend = min(kend, j0 + BN);
+  if (fl & G_TRI_A_UPPER) kbeg = max(kbeg, (i0 / BK) * BK);
+  if (fl & G_TRI_B_LOWER) kbeg = max(kbeg, (j0 / BK) * BK);
+
+  const T* A = g.A + d.a;   // may alias C (in-place panel update)
+  const T* __restrict__ B = g.B + d.b;
+  const bool ta = fl & G_TRANS_A, tb = fl & G_TRANS_B;
+  const int tid = threadIdx.x;
+  const int tx = tid % NTX, ty = tid / NTX;
+
+  T ra[LA], rb[LB];
+  auto load = [&](int kt) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      int idx = tid + q * NT;
+      int r, c;
+      if (!ta) { r = idx % BM; c = idx / BM; } else { c = idx % BK; r = idx / BK; }
+      int gi = i0 + r, gk = kt + c;
+      bool ok = gi < d.m && gk < kend && gk >= 0;
+      if ((fl & G_TRI_A_LOWER) && gk > gi) ok = false;
+      if ((fl & G_TRI_A_UPPER) && gk < gi) ok = false;
+      T v = T(0);
+      if (ok) v = ta ? A[gk + (int64_t)gi * d.lda] : A[gi + (int64_t)gk * d.lda];
+      ra[q] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      int idx = tid + q * NT;
+      int c, j;
+      if (!tb) { c = idx % BK; j = idx / BK; } else { j = idx % BN; c = idx / BN; }
+      int gk = kt + c, gj = j0 + j;
+      bool ok = gj < d.n && gk < kend && gk >= 0;
+      if ((fl & G_TRI_B_LOWER) && gk < gj) ok = false;
+      if ((fl & G_TRI_B_UPPER) && gk > gj) ok = false;
+      T v = T(0);
+      if (ok) v = tb ? B[gj + (int64_t)gk * d.ldb] : B[gk + (int64_t)gj * d.ldb];
+      rb[q] = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      int idx = tid + q * NT;
+      int r, c;
+      if (!ta) { r = idx % BM; c = idx / BM; } else { c = idx % BK; r = idx / BK; }
+      As[buf][c][r] = ra[q];
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      int idx = tid + q * NT;
+      int c, j;
+      if (!tb) { c = idx % BK; j = idx / BK; } else { j = idx % BN; c = idx / BN; }
+      Bs[buf][c][j] = rb[q];
+    }
+  };
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int p = 0; p < TM; ++p)
+#pragma unroll
+    for (int q = 0; q < TN; ++q) acc[p][q] = T(0);
+
+  using V = typename Vec2<T>::type;
+  constexpr int W = Vec2<T>::W;
+  int buf = 0;
+  if (kbeg < kend) {
+    load(kbeg);
+    store(0);
+    __syncthreads();
+    for (int kt = kbeg; kt < kend; kt += BK) {
+      const bool more = kt + BK < kend;
+      if (more) load(kt + BK);
+#pragma unroll
+      for (int kk = 0; kk < BK; ++kk) {
+        T a[TM], b[TN];
+#pragma unroll
+        for (int p = 0; p < TM; p += W) {
+          V v = *reinterpret_cast<const V*>(&As[buf][kk][tx * TM + p]);
+          memcpy(&a[p], &v, sizeof(V));
+        }
+#pragma unroll
+        for (int q = 0; q < TN; q += W) {
+          V v = *reinterpret_cast<const V*>(&Bs[buf][kk][ty * TN + q]);
+          memcpy(&b[q], &v, sizeof(V));
+        }
+#pragma unroll
+        for (int p = 0; p < TM; ++p)
+#pragma unroll
+          for (int q = 0; q < TN; ++q) acc[p][q] = fma(a[p], b[q], acc[p][q]);
+      }
+      if (more) {
+        store(buf ^ 1);
+        __syncthreads();
+        buf ^= 1;
+      }
+    }
+  }
+
+  T* C = g.C + d.c;
+  const bool lower = fl & G_OUT_LOWER;
+#pragma unroll
+  for (int q = 0; q < TN; ++q) {
+    int j = j0 + ty * TN + q;
+    if (j >= d.n) continue;
+#pragma unroll
+    for (int p = 0; p < TM; ++p) {
+      int i = i0 + tx * TM + p;
+      if (i >= d.m || (lower && i < j)) continue;
+      int64_t o = i + (int64_t)j * d.ldc;
+      T v = g.alpha * acc[p][q];
+      if (g.beta != T(0)) v = fma(g.beta, C[o], v);
+      C[o] = v;
+    }
+  }
+}
+
+template <typename T> struct GemmTile;
+template <> struct GemmTile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
+template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
+
+template <typename T>
+void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
+                  T alpha, T beta, const T* A, const T* B, T* C) {
+  using TL = GemmTile<T>;
+  std::vector<GemmDesc> dd;
+  std::vector<int> prefix;
+  dd.reserve(d.size());
+  prefix.reserve(d.size() + 1);
+  int64_t total = 0;
+  for (const auto& x : d) {
+    if (x.m <= 0 || x.n <= 0) continue;
+    dd.push_back(x);
+    prefix.push_back((int)total);
+    total += (int64_t)((x.m + TL::BM - 1) / TL::BM) * ((x.n + TL::BN - 1) / TL::BN);
+  }
+  if (dd.empty()) return;
+  AMB_CHECK(total < (int64_t)1 << 31, AMB_EINVAL, "GEMM batch too large");
+  prefix.push_back((int)total);
+  // one staging push: descriptors then prefix
+  std::vector<char> blob(dd.size() * sizeof(GemmDesc) + prefix.size() * sizeof(int));
+  memcpy(blob.data(), dd.data(), dd.size() * sizeof(GemmDesc));
+  memcpy(blob.data() + dd.size() * sizeof(GemmDesc), prefix.data(), prefix.size() * sizeof(int));
+  char* dev = static_cast<char*>(ring.push(blob.data(), blob.size(), st));
+  GemmArgs<T> g;
+  g.desc = reinterpret_cast<const GemmDesc*>(dev);
+  g.prefix = reinterpret_cast<const int*>(dev + dd.size() * sizeof(GemmDesc));
+  g.ndesc = (int)dd.size();
+  g.flags = flags;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
+  k_gemm<T, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
+  AMB_LAUNCHED();
+}
+
+template void gemm_batched<float>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, float, float,
+                                  const float*, const float*, float*);
+template void gemm_batched<double>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, double, double,
+                                   const double*, const double*, double*);
+
+// ------------------------------------------------------------------ GEMV
+// y = alpha op(A) x + beta y, one vector per descriptor.  No-transpose:
+// one thread per row, columns streamed (coalesced along rows); transpose:
+// one warp per output, lanes stride down the column.
+
+template <typename T>
+struct GemvArgs {
+  const GemvDesc* desc;
+  const int* prefix;
+  int ndesc, flags;
+  T alpha, beta;
+  const T* A;
+  const T* X;
+  T* Y;
+};
+
+constexpr int kGemvRows = 256;   // rows per CTA (no-transpose)
+constexpr int kGemvCols = 8;     // outputs per CTA (transpose): one warp each
+
+template <typename T>
+__device__ inline int gemv_find(const GemvArgs<T>& g, int bid) {
+  int lo = 0, hi = g.ndesc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.prefix[mid] <= bid) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kGemvRows) k_gemv_n(GemvArgs<T> g) {
+  __shared__ T xs[1024];
+  const int di = gemv_find(g, blockIdx.x);
+  const GemvDesc d = g.desc[di];
+  const int i = (blockIdx.x - g.prefix[di]) * kGemvRows + threadIdx.x;
+  const T* __restrict__ A = g.A + d.a;
+  const T* __restrict__ x = g.X + d.x;
+  int lend = d.n;
+  if (g.flags & G_TRI_A_LOWER) lend = min(d.n, (blockIdx.x - g.prefix[di]) * kGemvRows + kGemvRows);
+  int lbeg = 0;
+  if (g.flags & G_TRI_A_UPPER) lbeg = (blockIdx.x - g.prefix[di]) * kGemvRows;
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  for (int c0 = lbeg; c0 < lend; c0 += 1024) {
+    int cn = min(1024, lend - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cn; q += kGemvRows) xs[q] = x[c0 + q];
+    __syncthreads();
+    if (i < d.m) {
+      int cl = 0, ch = cn;
+      if (g.flags & G_TRI_A_LOWER) ch = min(cn, i - c0 + 1);
+      if (g.flags & G_TRI_A_UPPER) cl = max(0, i - c0);
+      const T* col = A + i + (int64_t)(c0 + cl) * d.lda;
+      int q = cl;
+      for (; q + 3 < ch; q += 4) {
+        s0 = fma(col[0], xs[q], s0);
+        s1 = fma(col[d.lda], xs[q + 1], s1);
+        s2 = fma(col[2 * (int64_t)d.lda], xs[q + 2], s2);
+        s3 = fma(col[3 * (int64_t)d.lda], xs[q + 3], s3);
+        col += 4 * (int64_t)d.lda;
+      }
+      for (; q < ch; ++q) {
+        s0 = fma(col[0], xs[q], s0);
+        col += d.lda;
+      }
+    }
+  }
+  if (i < d.m) {
+    T v = g.alpha * ((s0 + s1) + (s2 + s3));
+    T* y = g.Y + d.y;
+    if (g.beta != T(0)) v = fma(g.beta, y[i], v);
+    y[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t(GemvArgs<T> g) {
+  const int di = gemv_find(g, blockIdx.x);
+  const GemvDesc d = g.desc[di];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = (blockIdx.x - g.prefix[di]) * kGemvCols + warp;   // output index = column of A
+  if (j >= d.n) return;
+  const T* __restrict__ col = g.A + d.a + (int64_t)j * d.lda;
+  const T* __restrict__ x = g.X + d.x;
+  int ib = 0, ie = d.m;
+  // op(A) = A^T; op(A) upper <=> A lower: only rows i >= j of column j
+  if (g.flags & G_TRI_A_UPPER) ib = min(j, d.m);
+  if (g.flags & G_TRI_A_LOWER) ie = min(d.m, j + 1);
+  T s0 = 0, s1 = 0;
+  int i = ib + lane;
+  for (; i + 32 < ie; i += 64) {
+    s0 = fma(col[i], x[i], s0);
+    s1 = fma(col[i + 32], x[i + 32], s1);
+  }
+  for (; i < ie; i += 32) s0 = fma(col[i], x[i], s0);
+  T s = s0 + s1;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    T v = g.alpha * s;
+    T* y = g.Y + d.y;
+    if (g.beta != T(0)) v = fma(g.beta, y[j], v);
+    y[j] = v;
+  }
+}
+
+template <typename T>
+void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& d, int flags,
+                  T alpha, T beta, const T* A, const T* X, T* Y) {
+  const bool trans = flags & G_TRANS_A;
+  std::vector<GemvDesc> dd;
+  std::vector<int> prefix;
+  int64_t total = 0;
+  for (const auto& x : d) {
+    int outs = trans ? x.n : x.m;
+    if (outs <= 0) continue;
+    dd.push_back(x);
+    prefix.push_back((int)total);
+    total += trans ? (outs + kGemvCols - 1) / kGemvCols : (outs + kGemvRows - 1) / kGemvRows;
+  }
+  if (dd.empty()) return;
+  prefix.push_back((int)total);
+  std::vector<char> blob(dd.size() * sizeof(GemvDesc) + prefix.size() * sizeof(int));
+  memcpy(blob.data(), dd.data(), dd.size() * sizeof(GemvDesc));
+  memcpy(blob.data() + dd.size() * sizeof(GemvDesc), prefix.data(), prefix.size() * sizeof(int));
+  char* dev = static_cast<char*>(ring.push(blob.data(), blob.size(), st));
+  GemvArgs<T> g{reinterpret_cast<const GemvDesc*>(dev),
+                reinterpret_cast<const int*>(dev + dd.size() * sizeof(GemvDesc)),
+                (int)dd.size(), flags, alpha, beta, A, X, Y};
+  if (trans) k_gemv_t<T><<<(unsigned)total, 32 * kGemvCols, 0, st>>>(g);
+  else k_gemv_n<T><<<(unsigned)total, kGemvRows, 0, st>>>(g);
+  AMB_LAUNCHED();
+}
+
+template void gemv_batched<float>(cudaStream_t, DescRing&, const std::vector<GemvDesc>&, int, float, float,
+                                  const float*, const float*, float*);
+template void gemv_batched<double>(cudaStream_t, DescRing&, const std::vector<GemvDesc>&, int, double, double,
+                                   const double*, const double*, double*);
+
+// ------------------------------------------------------------------ Cholesky
+// Diagonal block: unblocked Cholesky in FP64 shared memory (whatever the
+// storage type), then the explicit inverse of the block.  A non-positive
+// pivot is recorded (status[0] = AMB_ENOTSPD, status[1] = id, status[2] =
+// global column) and replaced by 1 so that the factorization stays finite.
+
+struct DiagDesc {
+  int64_t blk;      // offset of the diagonal block in the matrix buffer
+  int64_t zblk;     // offset of the inverse block in the Z buffer (-1: none)
+  int64_t scratch;  // offset (elements) of the nb x nb inverse in the scratch buffer
+  int32_t ld, zld, jb, id, col;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_diag(const DiagDesc* descs, T* base, T* zbase, T* scratch, int* status) {
+  __shared__ double a[kNB][kNB + 1];
+  const DiagDesc d = descs[blockIdx.x];
+  const int jb = d.jb, tid = threadIdx.x;
+  T* blk = base + d.blk;
+  for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+    int r = idx % jb, c = idx / jb;
+    a[r][c] = (r >= c) ? (double)blk[r + (int64_t)c * d.ld] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < jb; ++c) {
+    if (tid == 0) {
+      double p = a[c][c];
+      if (!(p > 0.0)) {
+        if (atomicCAS(status, 0, AMB_ENOTSPD) == 0) {
+          status[1] = d.id;
+          status[2] = d.col + c;
+        }
+        p = 1.0;
+      }
+      a[c][c] = sqrt(p);
+    }
+    __syncthreads();
+    const double piv = a[c][c];
+    for (int r = c + 1 + tid; r < jb; r += blockDim.x) a[r][c] /= piv;
+    __syncthreads();
+    const int m = jb - c - 1;
+    for (int idx = tid; idx < m * m; idx += blockDim.x) {
+      int r = c + 1 + idx % m, q = c + 1 + idx / m;
+      if (r >= q) a[r][q] -= a[r][c] * a[q][c];
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < jb * jb; idx += blockDim.x) {
+    int r = idx % jb, c = idx / jb;
+    if (r >= c) blk[r + (int64_t)c * d.ld] = (T)a[r][c];
+  }
+  // Inverse of the lower-triangular block by forward substitution, one
+  // column per thread; entry (i, j), i > j, of the inverse is kept in the
+  // unused upper triangle a[j][i], its diagonal in dinv[].
+  __shared__ double dinv[kNB];
+  if (tid < jb) {
+    const int j = tid;
+    dinv[j] = 1.0 / a[j][j];
+    for (int i = j + 1; i < jb; ++i) {
+      double s = a[i][j] * dinv[j];
+      for (int l = j + 1; l < i; ++l) s += a[i][l] * a[j][l];
+      a[j][i] = -s / a[i][i];
+    }
+  }
+  __syncthreads();
+  T* sc = scratch + d.scratch;
+  for (int idx = tid; idx < kNB * kNB; idx += blockDim.x) {
+    int r = idx % kNB, c = idx / kNB;
+    double v = 0.0;
+    if (r < jb && c < jb) v = (r > c) ? a[c][r] : (r == c ? dinv[r] : 0.0);
+    sc[r + c * kNB] = (T)v;
+    if (d.zblk >= 0 && r < jb && c < jb) zbase[d.zblk + r + (int64_t)c * d.zld] = (T)v;
+  }
+}
+
+// scratch space for the diagonal inverses, grown on demand
+template <typename T>
+static T* diag_scratch(size_t nblocks) {
+  static thread_local DevBuf buf;
+  size_t need = nblocks * kNB * kNB * sizeof(T);
+  if (buf.bytes < need) {
+    AMB_CUDA(cudaDeviceSynchronize());   // earlier factorizations may still read the old buffer
+    buf.alloc(need);
+  }
+  return dptr<T>(buf);
+}
+
+template <typename T>
+void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDesc>& d, T* base,
+                      T* zbase, int* status, double* flops) {
+  if (d.empty()) return;
+  int maxsteps = 0;
+  for (const auto& x : d) maxsteps = std::max(maxsteps, (x.c1 - x.c0 + kNB - 1) / kNB);
+  T* scratch = diag_scratch<T>(d.size());
+  for (int step = 0; step < maxsteps; ++step) {
+    std::vector<DiagDesc> dg;
+    std::vector<GemmDesc> panel, trail;
+    for (size_t q = 0; q < d.size(); ++q) {
+      const CholDesc& x = d[q];
+      const int j0 = x.c0 + step * kNB;
+      if (j0 >= x.c1) continue;
+      const int jb = std::min(kNB, x.c1 - j0);
+      DiagDesc g;
+      g.blk = x.off + j0 + (int64_t)j0 * x.ld;
+      g.zblk = zbase ? x.zoff + (int64_t)step * kNB * (x.zld + 1) : -1;
+      g.scratch = (int64_t)q * kNB * kNB;
+      g.ld = x.ld;
+      g.zld = x.zld;
+      g.jb = jb;
+      g.id = x.id;
+      g.col = j0;
+      dg.push_back(g);
+      const int r0 = j0 + jb, rem = x.n - r0;
+      if (rem > 0) {
+        // panel: P := P * Dinv^T  (rows r0.., columns j0..j0+jb), in place
+        GemmDesc p{rem, jb, jb, x.ld, kNB, x.ld, x.off + r0 + (int64_t)j0 * x.ld, (int64_t)q * kNB * kNB,
+                   x.off + r0 + (int64_t)j0 * x.ld};
+        panel.push_back(p);
+        // trailing lower update: C -= P P^T
+        GemmDesc u{rem, rem, jb, x.ld, x.ld, x.ld, x.off + r0 + (int64_t)j0 * x.ld,
+                   x.off + r0 + (int64_t)j0 * x.ld, x.off + r0 + (int64_t)r0 * x.ld};
+        trail.push_back(u);
+        if (flops) *flops += (double)rem * jb * jb + (double)rem * (rem + 1) * jb;
+      }
+      if (flops) *flops += (double)jb * jb * jb / 3.0;
+    }
+    if (dg.empty()) break;
+    const DiagDesc* ddev = static_cast<const DiagDesc*>(ring.push(dg.data(), dg.size() * sizeof(DiagDesc), st));
+    k_chol_diag<T><<<(unsigned)dg.size(), 256, 0, st>>>(ddev, base, zbase, scratch, status);
+    AMB_LAUNCHED();
+    if (!panel.empty()) {
+      gemm_batched<T>(st, ring, panel, G_TRANS_B | G_TRI_B_UPPER, T(1), T(0), base, scratch, base);
+      gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
+    }
+  }
+}
+
+template void partial_cholesky<float>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, float*, float*, int*, double*);
+template void partial_cholesky<double>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, double*, double*, int*, double*);
+
+// ------------------------------------------------------------------ TRTRI
+// [L11 0; L21 L22]^{-1} = [Z11 0; -Z22 L21 Z11, Z22], merged bottom-up from
+// the nb x nb diagonal inverses.  The upper block Z12 (unused by a lower
+// inverse) holds the intermediate (L21 Z11)^T.
+
+template <typename T>
+void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriDesc>& d, const T* lbase,
+                       T* zbase, double* flops) {
+  int maxn = 0;
+  for (const auto& x : d) maxn = std::max(maxn, x.n);
+  for (int half = kNB; half < maxn; half *= 2) {
+    const int b = 2 * half;
+    std::vector<GemmDesc> sa, sb;
+    for (const auto& x : d) {
+      for (int p0 = 0; p0 + half < x.n; p0 += b) {
+        const int h = p0 + half;
+        const int r2 = std::min(p0 + b, x.n) - h;
+        const int c1 = half;
+        // Z12 (c1 x r2) := Z11^T (upper) * L21^T
+        sa.push_back(GemmDesc{c1, r2, c1, x.zld, x.ld, x.zld, x.z + p0 + (int64_t)p0 * x.zld,
+                              x.l + h + (int64_t)p0 * x.ld, x.z + p0 + (int64_t)h * x.zld});
+        // Z21 (r2 x c1) := -Z22 (lower) * Z12^T
+        sb.push_back(GemmDesc{r2, c1, r2, x.zld, x.zld, x.zld, x.z + h + (int64_t)h * x.zld,
+                              x.z + p0 + (int64_t)h * x.zld, x.z + h + (int64_t)p0 * x.zld});
+        if (flops) *flops += (double)c1 * c1 * r2 + (double)r2 * r2 * c1;
+      }
+    }
+    if (sa.empty()) continue;
+    gemm_batched<T>(st, ring, sa, G_TRANS_A | G_TRI_A_UPPER | G_TRANS_B, T(1), T(0), zbase, lbase, zbase);
+    gemm_batched<T>(st, ring, sb, G_TRI_A_LOWER | G_TRANS_B, T(-1), T(0), zbase, zbase, zbase);
+  }
+}
+
+template void trtri_from_blocks<float>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const float*, float*, double*);
+template void trtri_from_blocks<double>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const double*, double*, double*);
+
+}  // namespace amb

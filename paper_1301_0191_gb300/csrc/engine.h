@@ -1,0 +1,90 @@
+// The batched substructure engine (one context, one GPU).
+#pragma once
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.h"
+#include "kernels.h"
+#include "level.h"
+#include "topology.h"
+
+namespace amb {
+
+struct Mesh {
+  int nx = 0, ny = 0, nz = 0, dpn = 1;
+  double h = 1.0, nu = 0.3;
+  int64_t nel = 0, nnodes = 0, ndof = 0;   // ndof = nnodes * dpn (full grid)
+  std::vector<uint8_t> dir_h;
+  std::vector<int32_t> elem_sub_h;
+  DevBuf coeff, dir, khat, elem_sub, elem_local;
+};
+
+struct PairReportH {
+  int level, s, t, n_computed, n_selected, n_rows, converged, iterations;
+  std::vector<double> lambda;
+};
+
+struct Timers {
+  double phase_ms[8] = {0};
+  double fam_ms[AMB_FAM_N] = {0};
+  int64_t fam_launches[AMB_FAM_N] = {0};
+  double fam_flops[AMB_FAM_N] = {0};
+  double fam_bytes[AMB_FAM_N] = {0};
+};
+
+// Event pair around a kernel family section (only when timing is enabled).
+struct FamTimer {
+  cudaStream_t st;
+  Timers* tm;
+  int fam;
+  bool on;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int64_t l0;
+  FamTimer(cudaStream_t s, Timers* t, int f, bool enabled) : st(s), tm(t), fam(f), on(enabled), l0(g_launches) {
+    if (on) {
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+    }
+  }
+  ~FamTimer() {
+    tm->fam_launches[fam] += g_launches - l0;
+    if (on) {
+      cudaEventRecord(b, st);
+      cudaEventSynchronize(b);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, a, b);
+      tm->fam_ms[fam] += ms;
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  }
+};
+
+class EngineBase {
+ public:
+  virtual ~EngineBase() = default;
+  virtual void setup() = 0;
+  virtual void precond(const double* r, double* z) = 0;   // device full-grid vectors
+  virtual void schur_apply(int level, int width, const void* x, void* y) = 0;
+  virtual const LevelTopo& topo(int level) const = 0;
+  virtual int n_levels() const = 0;
+  virtual void export_sub(int what, int level, int idx, std::vector<char>& out) = 0;
+  virtual double level_factor_flops(int level) const = 0;
+};
+
+struct EngineConfig {
+  amb_options opt;
+  int levels = 2;
+  double tau = 10.0;
+  std::vector<std::vector<int32_t>> parents;
+  std::vector<int> nsubs;   // per level (index 0 = level 1)
+};
+
+std::unique_ptr<EngineBase> make_engine(int precision, Mesh& mesh, const EngineConfig& cfg, cudaStream_t st,
+                                        DescRing& ring, Timers& tm, std::vector<PairReportH>& reports,
+                                        std::vector<double>& omega, std::vector<int>& nadapt, DevBuf& status);
+
+}  // namespace amb

@@ -1,0 +1,991 @@
+// Adaptive selection of face constraints on one level (Sec. 4, 5, 7.2):
+// all pair eigenproblems of the level run in lockstep as one batch.
+//
+// For a pair (s, t) the vectors live on Gamma^s + Gamma^t (two interface
+// copies, length N = n_g^s + n_g^t).  With shared dofs f, pair weights
+// d_s = K^s_jj/(K^s_jj + K^t_jj), d_t = 1 - d_s (Sec. 7.2) and the jump
+// j = w^s_f - w^t_f:
+//   (I - E) w          = [ d_t j on f (s copy) ; -d_s j on f (t copy) ], 0 elsewhere
+//   (I - E)^T v        = [ x ; -x ] on f,  x = d_t v^s_f - d_s v^t_f
+//   Pi                 = I - D^T (D D^T)^{-1} D, D = jump rows of the initial
+//                        coarse dofs shared by s and t; their supports are
+//                        disjoint, so Pi acts group by group
+//   A  = Pi (I-E)^T S (I-E) Pi   (only S_ff of each side is touched)
+//   B  = Pi S Pi
+//   M  = Pi ( Neumann^s + Neumann^t + Psi (Psi^T S Psi)^+ Psi^T ) Pi   (eq. bddc_pair)
+// LOBPCG (block size m) finds the m largest eigenpairs of A w = lambda B w
+// in the factor space modulo null(B) (eq. eig-nullspace): Rayleigh-Ritz on
+// [X W P] with FP64 Gram matrices and an SVQB B-orthonormalization that
+// drops directions of negligible B-norm.  Rows c_l = A w_l (eq. d-def) for
+// lambda_l > tau, restricted to the face dofs, orthonormalized (Sec. 7.2).
+#include <cmath>
+
+#include "engine_impl.h"
+
+namespace amb {
+
+namespace {
+
+enum PairField {
+  Q_S, Q_T, Q_NS, Q_NT, Q_N, Q_NF, Q_OQ, Q_OT, Q_OJ, Q_OF, Q_FOFF, Q_GBEG, Q_GEND, Q_FACEOFF, Q_FACEN,
+  Q_CMS, Q_CMT, Q_NCP, Q_NCS, Q_NCT, Q_OC, Q_OPI, Q_OGR, Q_OCC, Q_OR, Q_NPAIRF
+};
+#define QP(p, f) qp[(int64_t)(p) * Q_NPAIRF + (f)]
+
+constexpr int kJacobiMax = 112;
+
+// ---------------------------------------------------------------- block helpers
+
+__device__ double block_sum(double v, double* red) {
+  const int tid = threadIdx.x;
+  red[tid] = v;
+  __syncthreads();
+  for (int o = blockDim.x >> 1; o > 0; o >>= 1) {
+    if (tid < o) red[tid] += red[tid + o];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in shared
+// memory (column-major, leading dimension ld).  Rotations of one round act
+// on disjoint index pairs (round-robin ordering) and are applied together.
+// On exit A holds the eigenvalues on its diagonal, V the eigenvectors.
+__device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, double* cs, double* sn, int* P,
+                           int* Q) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    int r = idx % n, c = idx / n;
+    V[r + c * ld] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (n <= 1) return;
+  const int ne = n + (n & 1), half = ne / 2;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int r = idx % n, c = idx / n;
+      double a = A[r + c * ld];
+      tot += a * a;
+      if (r != c) off += a * a;
+    }
+    off = block_sum(off, red);
+    tot = block_sum(tot, red);
+    if (off <= 1e-30 * tot || tot == 0.0) break;
+    for (int round = 0; round < ne - 1; ++round) {
+      for (int k = tid; k < half; k += nt) {
+        int a = (k == 0) ? 0 : 1 + ((k - 1 + round) % (ne - 1));
+        int b = 1 + ((ne - 2 - k + round) % (ne - 1));
+        int p = a < b ? a : b, q = a < b ? b : a;
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          double apq = A[p + q * ld];
+          double app = A[p + p * ld], aqq = A[q + q * ld];
+          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
+            double th = (aqq - app) / (2.0 * apq);
+            double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        P[k] = q < n ? p : -1;
+        Q[k] = q;
+        cs[k] = c;
+        sn[k] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {
+        int k = idx / n, j = idx % n;
+        int p = P[k];
+        if (p < 0 || sn[k] == 0.0) continue;
+        int q = Q[k];
+        double c = cs[k], s = sn[k];
+        double apj = A[p + j * ld], aqj = A[q + j * ld];
+        A[p + j * ld] = c * apj - s * aqj;
+        A[q + j * ld] = s * apj + c * aqj;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < half * n; idx += nt) {
+        int k = idx / n, i = idx % n;
+        int p = P[k];
+        if (p < 0 || sn[k] == 0.0) continue;
+        int q = Q[k];
+        double c = cs[k], s = sn[k];
+        double aip = A[i + p * ld], aiq = A[i + q * ld];
+        A[i + p * ld] = c * aip - s * aiq;
+        A[i + q * ld] = s * aip + c * aiq;
+        double vip = V[i + p * ld], viq = V[i + q * ld];
+        V[i + p * ld] = c * vip - s * viq;
+        V[i + q * ld] = s * vip + c * viq;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// descending order of the diagonal of A (n <= kJacobiMax), by one thread
+__device__ void sort_desc(const double* A, int n, int ld, int* ord) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    for (int i = 0; i < n; ++i) {
+      int b = i;
+      for (int j = i + 1; j < n; ++j)
+        if (A[ord[j] + ord[j] * ld] > A[ord[b] + ord[b] * ld]) b = j;
+      int t = ord[i];
+      ord[i] = ord[b];
+      ord[b] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- pair kernels
+
+// pseudo-random start block (counter-based hash, SplitMix64 finalizer)
+__device__ inline double hash_uniform(uint64_t x) {
+  x += 0x9E3779B97F4A7C15ull;
+  x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+  x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+  x ^= x >> 31;
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+template <typename T>
+__global__ void k_lob_random(T* Qb, const int64_t* qp, int m, uint64_t seed) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * 9 * m) return;
+  const int64_t col = idx / N;
+  T v = T(0);
+  if (col < m) v = (T)hash_uniform(seed * 0x100000001B3ull ^ ((uint64_t)p << 40) ^ (uint64_t)idx);
+  Qb[QP(p, Q_OQ) + idx] = v;
+}
+
+// Pi on columns [c0, c0+w) of a block with leading dimension N at base
+// offset QP(p, which) (+ c0*N).  One warp per (group, column).
+template <typename T>
+__global__ void k_lob_project(T* base, const int64_t* qp, int which, int c0, int w, const int32_t* goff,
+                              const int32_t* gent, const T* gw, const int32_t* ps, const int32_t* pt) {
+  const int p = blockIdx.x;
+  const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS);
+  const int64_t g0 = QP(p, Q_GBEG), g1 = QP(p, Q_GEND), foff = QP(p, Q_FOFF);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t ngr = g1 - g0;
+  for (int64_t job = warp; job < ngr * w; job += nw) {
+    const int64_t g = g0 + job % ngr;
+    const int col = c0 + (int)(job / ngr);
+    T* v = base + QP(p, which) + (int64_t)col * N;
+    double num = 0.0, den = 0.0;
+    for (int e = goff[g] + lane; e < goff[g + 1]; e += 32) {
+      const int f = gent[e];
+      const double c = (double)gw[e];
+      num += c * ((double)v[ps[foff + f]] - (double)v[ns + pt[foff + f]]);
+      den += c * c;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      num += __shfl_xor_sync(0xffffffffu, num, o);
+      den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    const double a = den > 0 ? num / (2.0 * den) : 0.0;
+    for (int e = goff[g] + lane; e < goff[g + 1]; e += 32) {
+      const int f = gent[e];
+      const double c = (double)gw[e];
+      v[ps[foff + f]] = (T)((double)v[ps[foff + f]] - c * a);
+      v[ns + pt[foff + f]] = (T)((double)v[ns + pt[foff + f]] + c * a);
+    }
+  }
+}
+
+// J_s = d_t * j, J_t = -d_s * j with j = v^s_f - v^t_f (nf x w each)
+template <typename T>
+__global__ void k_lob_jump(T* J, const T* base, const int64_t* qp, int which, int c0, int w, const int32_t* ps,
+                           const int32_t* pt, const T* ws, const T* wt) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS), nf = QP(p, Q_NF), foff = QP(p, Q_FOFF);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nf * w) return;
+  const int64_t f = idx % nf, col = idx / nf;
+  const T* v = base + QP(p, which) + (c0 + col) * N;
+  const T j = v[ps[foff + f]] - v[ns + pt[foff + f]];
+  T* Jb = J + QP(p, Q_OJ);
+  Jb[f + col * nf] = wt[foff + f] * j;
+  Jb[nf * w + f + col * nf] = -ws[foff + f] * j;
+}
+
+// out = (I - E)^T [Y_s ; Y_t] scattered on f (s copy x, t copy -x), zero elsewhere
+template <typename T>
+__global__ void k_lob_iet(T* base, const int64_t* qp, int which, int c0, const T* J, int w, const int32_t* ps,
+                          const int32_t* pt, const T* ws, const T* wt) {
+  const int p = blockIdx.x, col = blockIdx.y;
+  const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS), nf = QP(p, Q_NF), foff = QP(p, Q_FOFF);
+  T* v = base + QP(p, which) + (int64_t)(c0 + col) * N;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) v[i] = T(0);
+  __syncthreads();
+  const T* Y = J + QP(p, Q_OJ) + 2 * nf * w;
+  for (int64_t f = threadIdx.x; f < nf; f += blockDim.x) {
+    const T x = wt[foff + f] * Y[f + col * nf] - ws[foff + f] * Y[nf * w + f + col * nf];
+    v[ps[foff + f]] = x;
+    v[ns + pt[foff + f]] = -x;
+  }
+}
+
+template <typename T>
+__global__ void k_lob_zero(T* base, const int64_t* qp, int which, int c0, int w) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * w) return;
+  base[QP(p, which) + c0 * N + idx] = T(0);
+}
+
+// coarse gather/scatter of the pair coarse space
+template <typename T>
+__global__ void k_lob_cgather(T* C, const int64_t* qp, int m, const int32_t* cms, const int32_t* cmt) {
+  const int p = blockIdx.x;
+  const int64_t ncp = QP(p, Q_NCP), ncs = QP(p, Q_NCS), nct = QP(p, Q_NCT), oc = QP(p, Q_OC);
+  T* cs = C + oc;
+  T* ct = cs + ncs * m;
+  T* cp = ct + nct * m;
+  for (int64_t i = threadIdx.x; i < ncp * m; i += blockDim.x) cp[i] = T(0);
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < ncs * m; i += blockDim.x) {
+    int64_t q = i % ncs, col = i / ncs;
+    cp[cms[QP(p, Q_CMS) + q] + col * ncp] += cs[i];
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < nct * m; i += blockDim.x) {
+    int64_t q = i % nct, col = i / nct;
+    cp[cmt[QP(p, Q_CMT) + q] + col * ncp] += ct[i];
+  }
+}
+template <typename T>
+__global__ void k_lob_cscatter(T* C, const int64_t* qp, int m, const int32_t* cms, const int32_t* cmt) {
+  const int p = blockIdx.x;
+  const int64_t ncp = QP(p, Q_NCP), ncs = QP(p, Q_NCS), nct = QP(p, Q_NCT), oc = QP(p, Q_OC);
+  T* cs = C + oc;
+  T* ct = cs + ncs * m;
+  const T* up = ct + nct * m + ncp * m;
+  T* us = (T*)up + ncp * m;
+  T* ut = us + ncs * m;
+  for (int64_t i = threadIdx.x; i < ncs * m; i += blockDim.x) {
+    int64_t q = i % ncs, col = i / ncs;
+    us[i] = up[cms[QP(p, Q_CMS) + q] + col * ncp];
+  }
+  for (int64_t i = threadIdx.x; i < nct * m; i += blockDim.x) {
+    int64_t q = i % nct, col = i / nct;
+    ut[i] = up[cmt[QP(p, Q_CMT) + q] + col * ncp];
+  }
+}
+
+// pseudo-inverse of the pair coarse matrix Psi^T S^{st} Psi (Sec. 5: dense
+// eigen-decomposition, eigenvalues below a tolerance dropped)
+template <typename T>
+__global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const int64_t* acs, const int64_t* act,
+                            const int32_t* cms, const int32_t* cmt, int* status) {
+  extern __shared__ double sh[];
+  const int p = blockIdx.x;
+  const int n = (int)QP(p, Q_NCP), ncs = (int)QP(p, Q_NCS), nct = (int)QP(p, Q_NCT);
+  double* A = sh;
+  double* V = A + n * n;
+  __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
+  __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) A[i] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* as = Ac + acs[p];
+    const double* at = Ac + act[p];
+    const int32_t* ms = cms + QP(p, Q_CMS);
+    const int32_t* mt = cmt + QP(p, Q_CMT);
+    for (int b = 0; b < ncs; ++b)
+      for (int a = 0; a < ncs; ++a) A[ms[a] + ms[b] * n] += as[a + b * ncs];
+    for (int b = 0; b < nct; ++b)
+      for (int a = 0; a < nct; ++a) A[mt[a] + mt[b] * n] += at[a + b * nct];
+  }
+  __syncthreads();
+  jacobi_eig(A, V, n, n, red, cs_, sn_, P_, Q_);
+  double mx = 0.0;
+  for (int i = 0; i < n; ++i) mx = fmax(mx, A[i + i * n]);
+  const double tol = 1e-12 * mx;
+  T* out = pinv + QP(p, Q_OPI);
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    int r = idx % n, c = idx / n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) {
+      double l = A[k + k * n];
+      if (l > tol) s += V[r + k * n] * V[c + k * n] / l;
+    }
+    out[idx] = (T)s;
+  }
+}
+
+// FP64 Gram matrices G = U^T V over the first w columns of the panel;
+// kind 0: V = A-block, kind 1: V = B-block.
+template <typename T>
+__global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int w) {
+  const int p = blockIdx.x, kind = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int m3 = 3 * m;
+  const T* U = Qb + QP(p, Q_OQ);
+  const T* Vb = U + (int64_t)(kind ? 6 * m : 3 * m) * N;
+  __shared__ double us[32][33], vs[32][33];
+  double acc[5] = {0, 0, 0, 0, 0};
+  const int nout = w * w;
+  for (int64_t r0 = 0; r0 < N; r0 += 32) {
+    const int rn = (N - r0) < 32 ? (int)(N - r0) : 32;
+    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
+      int r = idx % 32, c = idx / 32;
+      us[r][c] = r < rn ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
+      vs[r][c] = r < rn ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
+    }
+    __syncthreads();
+    for (int q = 0; q < 5; ++q) {
+      int o = threadIdx.x + q * blockDim.x;
+      if (o >= nout) break;
+      int a = o % w, b = o / w;
+      double s = acc[q];
+      for (int r = 0; r < rn; ++r) s = fma(us[r][a], vs[r][b], s);
+      acc[q] = s;
+    }
+    __syncthreads();
+  }
+  double* g = G + QP(p, Q_OGR) + (int64_t)kind * m3 * m3;
+  for (int q = 0; q < 5; ++q) {
+    int o = threadIdx.x + q * blockDim.x;
+    if (o >= nout) break;
+    int a = o % w, b = o / w;
+    g[a + b * m3] = acc[q];
+  }
+}
+
+// Rayleigh-Ritz on the width-w basis: SVQB with column scaling, then the
+// reduced standard eigenproblem; coefficients Cc = [Cx | Cp] (3m x 2m, T)
+// and the m largest Ritz values.  Frozen pairs keep X (Cx = I, Cp = 0).
+template <typename T>
+__global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w) {
+  extern __shared__ double sh[];
+  const int p = blockIdx.x;
+  const int m3 = 3 * m;
+  double* GA = sh;
+  double* GB = GA + w * w;
+  double* V = GB + w * w;
+  double* Mr = V + w * w;
+  double* Yr = Mr + w * w;
+  double* dsc = Yr + w * w;   // w
+  __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
+  __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1], ord[kJacobiMax], ord2[kJacobiMax];
+  __shared__ int rank_sh;
+  T* C = Cc + QP(p, Q_OCC);
+  double* L = lam + (int64_t)p * m;
+  if (!active[p]) {
+    for (int idx = threadIdx.x; idx < m3 * 2 * m; idx += blockDim.x) {
+      int r = idx % m3, c = idx / m3;
+      C[idx] = (c < m && r == c) ? T(1) : T(0);
+    }
+    return;
+  }
+  const double* ga = G + QP(p, Q_OGR);
+  const double* gb = ga + m3 * m3;
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    int r = idx % w, c = idx / w;
+    GA[idx] = 0.5 * (ga[r + c * m3] + ga[c + r * m3]);
+    GB[idx] = 0.5 * (gb[r + c * m3] + gb[c + r * m3]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double dmax = 0.0;
+    for (int i = 0; i < w; ++i) dmax = fmax(dmax, GB[i + i * w]);
+    for (int i = 0; i < w; ++i) {
+      double d = GB[i + i * w];
+      dsc[i] = (d > 1e-14 * dmax && d > 0.0) ? 1.0 / sqrt(d) : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    int r = idx % w, c = idx / w;
+    GA[idx] *= dsc[r] * dsc[c];
+    GB[idx] *= dsc[r] * dsc[c];
+  }
+  __syncthreads();
+  jacobi_eig(GB, V, w, w, red, cs_, sn_, P_, Q_);
+  sort_desc(GB, w, w, ord);
+  if (threadIdx.x == 0) {
+    double smax = GB[ord[0] + ord[0] * w];
+    int r = 0;
+    while (r < w && GB[ord[r] + ord[r] * w] > 1e-10 * smax && smax > 0.0) ++r;
+    rank_sh = r;
+  }
+  __syncthreads();
+  const int r = rank_sh;
+  // Tm = V[:, ord[:r]] diag(sigma^{-1/2}) stored in Yr (w x r)
+  for (int idx = threadIdx.x; idx < w * r; idx += blockDim.x) {
+    int i = idx % w, k = idx / w;
+    int c = ord[k];
+    Yr[i + k * w] = V[i + c * w] / sqrt(GB[c + c * w]);
+  }
+  __syncthreads();
+  // V := GA Tm (w x r), then Mr := Tm^T V (r x r)
+  for (int idx = threadIdx.x; idx < w * r; idx += blockDim.x) {
+    int i = idx % w, k = idx / w;
+    double s = 0.0;
+    for (int j = 0; j < w; ++j) s += GA[i + j * w] * Yr[j + k * w];
+    V[i + k * w] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    int a = idx % r, b = idx / r;
+    double s = 0.0;
+    for (int j = 0; j < w; ++j) s += Yr[j + a * w] * V[j + b * w];
+    Mr[a + b * r] = s;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
+    int a = idx % r, b = idx / r;
+    if (a > b) {
+      double s = 0.5 * (Mr[a + b * r] + Mr[b + a * r]);
+      Mr[a + b * r] = s;
+      Mr[b + a * r] = s;
+    }
+  }
+  __syncthreads();
+  jacobi_eig(Mr, GB, r, r, red, cs_, sn_, P_, Q_);   // eigenvectors into GB (r x r, ld r)
+  sort_desc(Mr, r, r, ord2);
+  const int mm = min(m, r);
+  // Cx(:, k) = D Tm y_k ; Cp = Cx with the X rows zeroed
+  for (int idx = threadIdx.x; idx < m3 * m; idx += blockDim.x) {
+    int i = idx % m3, k = idx / m3;
+    double s = 0.0;
+    if (i < w && k < mm) {
+      int c = ord2[k];
+      for (int j = 0; j < r; ++j) s += Yr[i + j * w] * GB[j + c * r];
+      s *= dsc[i];
+    }
+    C[i + (int64_t)k * m3] = (T)s;
+    C[i + (int64_t)(m + k) * m3] = (i < m) ? T(0) : (T)s;
+  }
+  if (threadIdx.x < m) {
+    int k = threadIdx.x;
+    L[k] = k < mm ? Mr[ord2[k] + ord2[k] * r] : 0.0;
+  }
+}
+
+// R = A X - B X diag(lambda) into the W slot; residual and B-norms per column
+template <typename T>
+__global__ void k_lob_resid(T* Qb, double* rn, double* bn, const double* lam, const int64_t* qp, int m) {
+  const int p = blockIdx.x, col = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  T* base = Qb + QP(p, Q_OQ);
+  const T* AX = base + (int64_t)(3 * m + col) * N;
+  const T* BX = base + (int64_t)(6 * m + col) * N;
+  T* R = base + (int64_t)(m + col) * N;
+  const T l = (T)lam[(int64_t)p * m + col];
+  __shared__ double red[256];
+  double s = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    T v = AX[i] - l * BX[i];
+    R[i] = v;
+    s += (double)v * (double)v;
+    b += (double)BX[i] * (double)BX[i];
+  }
+  s = block_sum(s, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    rn[(int64_t)p * m + col] = sqrt(s);
+    bn[(int64_t)p * m + col] = sqrt(b);
+  }
+}
+
+// copy the updated blocks back: Tp = [Xn Pn | AXn APn | BXn BPn] -> panel
+template <typename T>
+__global__ void k_lob_copyback(T* Qb, const T* Tp, const int64_t* qp, int m) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * 6 * m) return;
+  const int64_t col = idx / N, row = idx % N;
+  const int grp = (int)(col / (2 * m)), within = (int)(col % (2 * m));
+  // within < m: X-type block (slot 0 of the group), else P-type (slot 2)
+  const int slot = grp * 3 + (within < m ? 0 : 2);
+  const int c = within % m;
+  Qb[QP(p, Q_OQ) + (int64_t)(slot * m + c) * N + row] = Tp[QP(p, Q_OT) + idx];
+}
+
+// adaptive rows: columns 0..k-1 of A X restricted to the face dofs (s copy),
+// orthonormalized by two passes of classical Gram-Schmidt; rows with a
+// negligible diagonal of R are dropped.
+template <typename T>
+__global__ void k_lob_rows(double* rows, int* kept, const T* Qb, const int64_t* qp, const int* nsel,
+                           const int32_t* ps, const int32_t* face, int m) {
+  const int p = blockIdx.x;
+  const int64_t N = QP(p, Q_N), foff = QP(p, Q_FOFF), nfc = QP(p, Q_FACEN), fco = QP(p, Q_FACEOFF);
+  const int k = nsel[p];
+  double* Rw = rows + QP(p, Q_OR);
+  const T* AX = Qb + QP(p, Q_OQ) + (int64_t)3 * m * N;
+  __shared__ double red[256], rkk[AMB_MAX_EIG];
+  for (int64_t idx = threadIdx.x; idx < nfc * k; idx += blockDim.x) {
+    int64_t e = idx % nfc, l = idx / nfc;
+    Rw[e + l * nfc] = (double)AX[ps[foff + face[fco + e]] + l * N];
+  }
+  __syncthreads();
+  for (int l = 0; l < k; ++l) {
+    double* v = Rw + (int64_t)l * nfc;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < l; ++j) {
+        const double* q = Rw + (int64_t)j * nfc;
+        double d = 0.0;
+        for (int64_t e = threadIdx.x; e < nfc; e += blockDim.x) d += q[e] * v[e];
+        d = block_sum(d, red);
+        if (rkk[j] == 0.0) d = 0.0;
+        for (int64_t e = threadIdx.x; e < nfc; e += blockDim.x) v[e] -= d * q[e];
+        __syncthreads();
+      }
+    }
+    double nrm = 0.0;
+    for (int64_t e = threadIdx.x; e < nfc; e += blockDim.x) nrm += v[e] * v[e];
+    nrm = sqrt(block_sum(nrm, red));
+    if (threadIdx.x == 0) rkk[l] = nrm;
+    __syncthreads();
+    const double sc = nrm > 0 ? 1.0 / nrm : 0.0;
+    for (int64_t e = threadIdx.x; e < nfc; e += blockDim.x) v[e] *= sc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int l = 0; l < k; ++l) mx = fmax(mx, rkk[l]);
+    int c = 0;
+    for (int l = 0; l < k; ++l) {
+      bool keep = rkk[l] >= 1e-10 * mx && mx > 0.0;
+      if (keep) {
+        if (c != l)
+          for (int64_t e = 0; e < nfc; ++e) Rw[e + c * nfc] = Rw[e + l * nfc];
+        ++c;
+      }
+    }
+    kept[p] = c;
+  }
+}
+
+template <typename T>
+__global__ void k_lob_copy_w(T* Tp, const T* Qb, const int64_t* qp, int m) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * m) return;
+  Tp[QP(p, Q_OT) + idx] = Qb[QP(p, Q_OQ) + (int64_t)m * N + idx];
+}
+
+inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
+
+}  // namespace
+
+// ---------------------------------------------------------------- driver
+
+template <typename T>
+void Engine<T>::adapt_level(LevelData<T>& L) {
+  FamTimer ftm(st, &tm, AMB_FAM_LOBPCG, timing());
+  LevelTopo& tp = L.topo;
+  const int np = (int)tp.pairs.size();
+  const int lvl = L.level;
+  if (np == 0) {
+    omega.push_back(0.0);
+    nadapt.push_back(0);
+    return;
+  }
+  const int maxad = std::max(0, cfg.opt.max_adaptive_per_face);
+  const int m = std::min(AMB_MAX_EIG, maxad + 1);
+  const int m3 = 3 * m;
+  // ------------------------------------------------ pair tables
+  std::vector<int64_t> qp((size_t)np * Q_NPAIRF, 0);
+  std::vector<int32_t> hps, hpt, hgoff(1, 0), hgent, hface, hcms, hcmt;
+  std::vector<double> hws, hwt, hgw;
+  std::vector<int64_t> acs(np), act(np);
+  std::vector<double> dg_h(L.vG.total);
+  AMB_CUDA(cudaMemcpyAsync(dg_h.data(), L.diagG.p, dg_h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMB_CUDA(cudaStreamSynchronize(st));
+  int64_t oQ = 0, oT = 0, oJ = 0, oF = 0, oC = 0, oPi = 0, oGr = 0, oCc = 0, oR = 0, oZ = 0, oQc = 0;
+  std::vector<int64_t> zoff(np), qcoff(np);
+  int max_ncp = 0;
+  for (int p = 0; p < np; ++p) {
+    const PairTopo& P = tp.pairs[p];
+    int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+    const int s = P.s, t = P.t;
+    const int64_t N = L.ng[s] + L.ng[t], nf = (int64_t)P.ps.size();
+    q[Q_S] = s;
+    q[Q_T] = t;
+    q[Q_NS] = L.ng[s];
+    q[Q_NT] = L.ng[t];
+    q[Q_N] = N;
+    q[Q_NF] = nf;
+    q[Q_OQ] = oQ;
+    oQ += N * 9 * m;
+    q[Q_OT] = oT;
+    oT += N * 6 * m;
+    q[Q_OJ] = oJ;
+    oJ += 4 * nf * m;
+    q[Q_OF] = oF;
+    oF += 2 * nf * nf;
+    q[Q_FOFF] = (int64_t)hps.size();
+    for (size_t e = 0; e < P.ps.size(); ++e) {
+      hps.push_back(P.ps[e]);
+      hpt.push_back(P.pt[e]);
+      const double ks = dg_h[L.vG.off[s] + P.ps[e]], kt = dg_h[L.vG.off[t] + P.pt[e]];
+      hws.push_back(ks / (ks + kt));
+      hwt.push_back(kt / (ks + kt));
+    }
+    q[Q_GBEG] = (int64_t)hgoff.size() - 1;
+    for (size_t g = 0; g + 1 < P.goff.size(); ++g) {
+      for (int e = P.goff[g]; e < P.goff[g + 1]; ++e) {
+        hgent.push_back(P.gent[e]);
+        hgw.push_back(P.gw[e]);
+      }
+      hgoff.push_back((int32_t)hgent.size());
+    }
+    q[Q_GEND] = (int64_t)hgoff.size() - 1;
+    q[Q_FACEOFF] = (int64_t)hface.size();
+    q[Q_FACEN] = (int64_t)P.face.size();
+    hface.insert(hface.end(), P.face.begin(), P.face.end());
+    q[Q_CMS] = (int64_t)hcms.size();
+    hcms.insert(hcms.end(), P.cmap_s.begin(), P.cmap_s.end());
+    q[Q_CMT] = (int64_t)hcmt.size();
+    hcmt.insert(hcmt.end(), P.cmap_t.begin(), P.cmap_t.end());
+    q[Q_NCP] = P.n_cpair;
+    q[Q_NCS] = L.nc[s];
+    q[Q_NCT] = L.nc[t];
+    max_ncp = std::max(max_ncp, P.n_cpair);
+    q[Q_OC] = oC;
+    oC += (int64_t)(2 * L.nc[s] + 2 * L.nc[t] + 2 * P.n_cpair) * m;
+    q[Q_OPI] = oPi;
+    oPi += (int64_t)P.n_cpair * P.n_cpair;
+    q[Q_OGR] = oGr;
+    oGr += 2LL * m3 * m3;
+    q[Q_OCC] = oCc;
+    oCc += (int64_t)m3 * 2 * m;
+    q[Q_OR] = oR;
+    oR += (int64_t)P.face.size() * m;
+    zoff[p] = oZ;
+    oZ += (int64_t)(L.nd[s] + L.nd[t]) * m;
+    qcoff[p] = oQc;
+    oQc += (int64_t)2 * (L.ncp[s] + L.ncp[t]) * m;
+    acs[p] = L.pAc.off[s];
+    act[p] = L.pAc.off[t];
+  }
+  AMB_CHECK(max_ncp <= kJacobiMax, AMB_EINVAL,
+            "pair coarse space larger than " + std::to_string(kJacobiMax) + " dofs");
+  DevBuf dqp, dps, dpt, dws, dwt, dgoff, dgent, dgw, dface, dcms, dcmt, dacs, dact;
+  upload(dqp, qp, st);
+  upload(dps, hps, st);
+  upload(dpt, hpt, st);
+  std::vector<T> tws(hws.begin(), hws.end()), twt(hwt.begin(), hwt.end()), tgw(hgw.begin(), hgw.end());
+  upload(dws, tws, st);
+  upload(dwt, twt, st);
+  upload(dgoff, hgoff, st);
+  upload(dgent, hgent, st);
+  upload(dgw, tgw, st);
+  upload(dface, hface, st);
+  upload(dcms, hcms, st);
+  upload(dcmt, hcmt, st);
+  upload(dacs, acs, st);
+  upload(dact, act, st);
+  DevBuf Qb, Tp, Jb, Sff, Zb, Qc, Cb, Pinv, Gr, Cc, lam, rn, bn, act_d, rows, kept, nsel_d;
+  Qb.alloc(oQ * sizeof(T));
+  Tp.alloc(oT * sizeof(T));
+  Jb.alloc(oJ * sizeof(T));
+  Sff.alloc(oF * sizeof(T));
+  Zb.alloc(oZ * sizeof(T));
+  Qc.alloc(oQc * sizeof(T));
+  Cb.alloc(oC * sizeof(T));
+  Pinv.alloc(oPi * sizeof(T));
+  Gr.alloc(oGr * sizeof(double));
+  Cc.alloc(oCc * sizeof(T));
+  lam.alloc((size_t)np * m * sizeof(double));
+  rn.alloc((size_t)np * m * sizeof(double));
+  bn.alloc((size_t)np * m * sizeof(double));
+  act_d.alloc(np * sizeof(int));
+  rows.alloc(std::max<int64_t>(oR, 1) * sizeof(double));
+  kept.alloc(np * sizeof(int));
+  nsel_d.alloc(np * sizeof(int));
+  AMB_CUDA(cudaMemsetAsync(Gr.p, 0, oGr * sizeof(double), st));
+  const int64_t* QPd = dptr<int64_t>(dqp);
+  T* Q = dptr<T>(Qb);
+  const T one = T(1), zero = T(0);
+
+  // S_ff of each side (gathered once)
+  {
+    std::vector<int64_t> so, sv;   // destination offset, source offset
+    for (int p = 0; p < np; ++p) {
+      const PairTopo& P = tp.pairs[p];
+      const int64_t nf = (int64_t)P.ps.size();
+      for (int side = 0; side < 2; ++side) {
+        const int sub = side ? P.t : P.s;
+        const auto& pos = side ? P.pt : P.ps;
+        for (int64_t b = 0; b < nf; ++b)
+          for (int64_t a = 0; a < nf; ++a) {
+            so.push_back(qp[(size_t)p * Q_NPAIRF + Q_OF] + side * nf * nf + a + b * nf);
+            sv.push_back(L.pS.off[sub] + pos[a] + (int64_t)pos[b] * L.ng[sub]);
+          }
+      }
+    }
+    DevBuf dso, dsv, tmpv;
+    upload(dso, so, st);
+    upload(dsv, sv, st);
+    tmpv.alloc(so.size() * sizeof(T));
+    gather<T, T>(st, dptr<T>(tmpv), dptr<T>(L.S), dptr<int64_t>(dsv), (int64_t)so.size());
+    scatter<T, T>(st, dptr<T>(Sff), dptr<T>(tmpv), dptr<int64_t>(dso), (int64_t)so.size());
+    AMB_CUDA(cudaStreamSynchronize(st));
+  }
+  // pseudo-inverse of the pair coarse matrices (initial constraints)
+  {
+    const size_t smem = (size_t)2 * max_ncp * max_ncp * sizeof(double);
+    AMB_CUDA(cudaFuncSetAttribute(k_pair_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
+    k_pair_pinv<T><<<np, 256, smem, st>>>(dptr<T>(Pinv), QPd, dptr<double>(L.Ac), dptr<int64_t>(dacs),
+                                          dptr<int64_t>(dact), dptr<int32_t>(dcms), dptr<int32_t>(dcmt), dptr<int>(status));
+    AMB_LAUNCHED();
+  }
+
+  // ------------------------------------------------ operators on panel column blocks
+  // slot indices (column offsets in units of m): X 0, W 1, P 2, AX 3, AW 4, AP 5, BX 6, BW 7, BP 8
+  auto project = [&](T* base, int which, int c0, int w) {
+    k_lob_project<T><<<np, 256, 0, st>>>(base, QPd, which, c0, w, dptr<int32_t>(dgoff), dptr<int32_t>(dgent),
+                                         dptr<T>(dgw), dptr<int32_t>(dps), dptr<int32_t>(dpt));
+    AMB_LAUNCHED();
+  };
+  int64_t maxN = 0, maxnf = 0;
+  for (int p = 0; p < np; ++p) {
+    maxN = std::max(maxN, qp[(size_t)p * Q_NPAIRF + Q_N]);
+    maxnf = std::max(maxnf, qp[(size_t)p * Q_NPAIRF + Q_NF]);
+  }
+  auto zero_block = [&](T* base, int which, int c0, int w) {
+    k_lob_zero<T><<<dim3(nblk(maxN * w), np), 256, 0, st>>>(base, QPd, which, c0, w);
+    AMB_LAUNCHED();
+  };
+  // out slot = A * (in slot); in and out are column blocks of the panel
+  auto applyA = [&](int cin, int cout) {
+    k_lob_jump<T><<<dim3(nblk(maxnf * m), np), 256, 0, st>>>(dptr<T>(Jb), Q, QPd, Q_OQ, cin * m, m, dptr<int32_t>(dps),
+                                                             dptr<int32_t>(dpt), dptr<T>(dws), dptr<T>(dwt));
+    AMB_LAUNCHED();
+    std::vector<GemmDesc> d;
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int nf = (int)q[Q_NF];
+      for (int side = 0; side < 2; ++side)
+        d.push_back(GemmDesc{nf, m, nf, std::max(nf, 1), std::max(nf, 1), std::max(nf, 1),
+                             q[Q_OF] + side * (int64_t)nf * nf, q[Q_OJ] + side * (int64_t)nf * m,
+                             q[Q_OJ] + (2 + side) * (int64_t)nf * m});
+    }
+    gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(Sff), dptr<T>(Jb), dptr<T>(Jb));
+    k_lob_iet<T><<<dim3(np, m), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, dptr<T>(Jb), m, dptr<int32_t>(dps),
+                                             dptr<int32_t>(dpt), dptr<T>(dws), dptr<T>(dwt));
+    AMB_LAUNCHED();
+    project(Q, Q_OQ, cout * m, m);
+  };
+  auto applyB = [&](int cin, int cout) {
+    std::vector<GemmDesc> d;
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int64_t N = q[Q_N];
+      for (int side = 0; side < 2; ++side) {
+        const int sub = (int)(side ? q[Q_T] : q[Q_S]);
+        const int ng = L.ng[sub];
+        const int64_t r0 = side ? q[Q_NS] : 0;
+        d.push_back(GemmDesc{ng, m, ng, std::max(ng, 1), (int)N, (int)N, L.pS.off[sub],
+                             q[Q_OQ] + cin * m * N + r0, q[Q_OQ] + cout * m * N + r0});
+      }
+    }
+    gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(L.S), Q, Q);
+    project(Q, Q_OQ, cout * m, m);
+  };
+  // W slot = M * (R in the temp panel, columns 0..m)
+  auto applyM = [&](int cout) {
+    project(dptr<T>(Tp), Q_OT, 0, m);
+    zero_block(Q, Q_OQ, cout * m, m);
+    std::vector<GemmDesc> d1, d2, d3, d4, d5, dc1, dc2, dpi;
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int64_t N = q[Q_N];
+      int64_t zo = zoff[p], qo = qcoff[p];
+      int64_t co = q[Q_OC];
+      for (int side = 0; side < 2; ++side) {
+        const int sub = (int)(side ? q[Q_T] : q[Q_S]);
+        const int nd = L.nd[sub], ncp = L.ncp[sub], nc = L.nc[sub], ng = L.ng[sub];
+        const int64_t r0 = side ? q[Q_NS] : 0;
+        const int64_t rin = q[Q_OT] + r0, rout = q[Q_OQ] + cout * m * N + r0;
+        const int ldd = std::max(nd, 1), ldc = std::max(ncp, 1);
+        // Neumann: z = L_D^{-1} r_D; qv = Y^T z; l = Ginv qv; z -= Y l; out_D = L_D^{-T} z
+        d1.push_back(GemmDesc{nd, m, nd, ldd, (int)N, ldd, L.pLD.off[sub], rin, zo});
+        d2.push_back(GemmDesc{ncp, m, nd, ldd, ldd, ldc, L.pY.off[sub], zo, qo});
+        d3.push_back(GemmDesc{ncp, m, ncp, ldc, ldc, ldc, L.pG.off[sub], qo, qo + (int64_t)ncp * m});
+        d4.push_back(GemmDesc{nd, m, ncp, ldd, ldc, ldd, L.pY.off[sub], qo + (int64_t)ncp * m, zo});
+        d5.push_back(GemmDesc{nd, m, nd, ldd, ldd, (int)N, L.pLD.off[sub], zo, rout});
+        // coarse: c = Psi^T r ; later out += Psi u
+        dc1.push_back(GemmDesc{nc, m, ng, std::max(ng, 1), (int)N, std::max(nc, 1), L.pPsi.off[sub], rin, co});
+        zo += (int64_t)nd * m;
+        qo += (int64_t)2 * ncp * m;
+        co += (int64_t)nc * m;
+      }
+    }
+    // the S-side and T-side blocks share base pointers: Zb for z, Qc for q/l, Cb for coarse
+    gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Tp), dptr<T>(Zb));
+    gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
+    gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
+    gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
+    gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), Q);
+    gemm_batched<T>(st, ring, dc1, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(Tp), dptr<T>(Cb));
+    k_lob_cgather<T><<<np, 256, 0, st>>>(dptr<T>(Cb), QPd, m, dptr<int32_t>(dcms), dptr<int32_t>(dcmt));
+    AMB_LAUNCHED();
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int ncpr = (int)q[Q_NCP];
+      const int64_t cp = q[Q_OC] + (q[Q_NCS] + q[Q_NCT]) * m;
+      dpi.push_back(GemmDesc{ncpr, m, ncpr, std::max(ncpr, 1), std::max(ncpr, 1), std::max(ncpr, 1), q[Q_OPI], cp,
+                             cp + (int64_t)ncpr * m});
+    }
+    gemm_batched<T>(st, ring, dpi, 0, one, zero, dptr<T>(Pinv), dptr<T>(Cb), dptr<T>(Cb));
+    k_lob_cscatter<T><<<np, 256, 0, st>>>(dptr<T>(Cb), QPd, m, dptr<int32_t>(dcms), dptr<int32_t>(dcmt));
+    AMB_LAUNCHED();
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int64_t N = q[Q_N];
+      const int64_t us = q[Q_OC] + (q[Q_NCS] + q[Q_NCT] + 2 * q[Q_NCP]) * m;
+      int64_t uo = us;
+      for (int side = 0; side < 2; ++side) {
+        const int sub = (int)(side ? q[Q_T] : q[Q_S]);
+        const int nc = L.nc[sub], ng = L.ng[sub];
+        const int64_t r0 = side ? q[Q_NS] : 0;
+        dc2.push_back(GemmDesc{ng, m, nc, std::max(ng, 1), std::max(nc, 1), (int)N, L.pPsi.off[sub], uo,
+                               q[Q_OQ] + cout * m * N + r0});
+        uo += (int64_t)nc * m;
+      }
+    }
+    gemm_batched<T>(st, ring, dc2, 0, one, one, dptr<T>(L.Psi), dptr<T>(Cb), Q);
+    project(Q, Q_OQ, cout * m, m);
+  };
+  auto rayleigh_ritz = [&](int w) {
+    k_lob_gram<T><<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), Q, QPd, m, w);
+    AMB_LAUNCHED();
+    const size_t smem = (size_t)(5 * w * w + w) * sizeof(double);
+    AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lob_rr<T><<<np, 256, smem, st>>>(dptr<T>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w);
+    AMB_LAUNCHED();
+    // [Xn Pn] = U Cc, [AXn APn] = AU Cc, [BXn BPn] = BU Cc
+    std::vector<GemmDesc> d;
+    for (int g = 0; g < 3; ++g) {
+      d.clear();
+      for (int p = 0; p < np; ++p) {
+        const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+        const int64_t N = q[Q_N];
+        d.push_back(GemmDesc{(int)N, 2 * m, w, (int)N, m3, (int)N, q[Q_OQ] + (int64_t)3 * g * m * N, q[Q_OCC],
+                             q[Q_OT] + (int64_t)2 * g * m * N});
+      }
+      gemm_batched<T>(st, ring, d, 0, one, zero, Q, dptr<T>(Cc), dptr<T>(Tp));
+    }
+    k_lob_copyback<T><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<T>(Tp), QPd, m);
+    AMB_LAUNCHED();
+  };
+
+  // ------------------------------------------------ LOBPCG
+  k_lob_random<T><<<dim3(nblk(maxN * 9 * m), np), 256, 0, st>>>(Q, QPd, m, cfg.opt.seed + 7919ull * lvl);
+  AMB_LAUNCHED();
+  std::vector<int> active(np, 1), iters(np, 0), conv(np, 0);
+  AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+  project(Q, Q_OQ, 0, m);
+  applyA(0, 3);
+  applyB(0, 6);
+  rayleigh_ritz(m);
+  std::vector<double> hl((size_t)np * m), hr((size_t)np * m), hb((size_t)np * m);
+  const double tol = cfg.opt.lobpcg_tol;
+  const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
+  const double tau = cfg.tau;
+  auto check = [&]() {
+    k_lob_resid<T><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m);
+    AMB_LAUNCHED();
+    AMB_CUDA(cudaMemcpyAsync(hl.data(), lam.p, hl.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMB_CUDA(cudaMemcpyAsync(hr.data(), rn.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMB_CUDA(cudaMemcpyAsync(hb.data(), bn.p, hb.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMB_CUDA(cudaStreamSynchronize(st));
+    int nact = 0;
+    for (int p = 0; p < np; ++p) {
+      bool ok = true;
+      const double lref = 0.1 * tau;
+      for (int k = 0; k < m; ++k) {
+        const double l = hl[(size_t)p * m + k];
+        const double b = hb[(size_t)p * m + k];
+        if (b == 0.0) continue;   // dropped direction (rank-deficient pair space)
+        if (!(hr[(size_t)p * m + k] <= tol * std::max(std::fabs(l), lref) * b)) ok = false;
+      }
+      conv[p] = ok ? 1 : 0;
+      active[p] = ok ? 0 : 1;
+      nact += active[p];
+    }
+    return nact;
+  };
+  int it = 0;
+  for (; it < maxit; ++it) {
+    const int nact = check();
+    if (nact == 0) break;
+    for (int p = 0; p < np; ++p) iters[p] += active[p];
+    AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    // R (W slot) -> temp panel columns 0..m, then W = M R
+    k_lob_copy_w<T><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<T>(Tp), Q, QPd, m);
+    AMB_LAUNCHED();
+    applyM(1);
+    applyA(1, 4);
+    applyB(1, 7);
+    rayleigh_ritz(it == 0 ? 2 * m : 3 * m);
+  }
+  check();
+  // ------------------------------------------------ selection and rows
+  std::vector<int> nsel(np, 0);
+  double om = 0.0;
+  for (int p = 0; p < np; ++p) {
+    int k = 0;
+    while (k < m && k < maxad && hl[(size_t)p * m + k] > tau) ++k;
+    nsel[p] = k;
+    const double next = k < m ? hl[(size_t)p * m + k] : 0.0;
+    om = std::max(om, next);
+  }
+  AMB_CUDA(cudaMemcpyAsync(nsel_d.p, nsel.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+  k_lob_rows<T><<<np, 256, 0, st>>>(dptr<double>(rows), dptr<int>(kept), Q, QPd, dptr<int>(nsel_d), dptr<int32_t>(dps),
+                                    dptr<int32_t>(dface), m);
+  AMB_LAUNCHED();
+  std::vector<double> hrows(std::max<int64_t>(oR, 1));
+  std::vector<int> hkept(np);
+  AMB_CUDA(cudaMemcpyAsync(hrows.data(), rows.p, hrows.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMB_CUDA(cudaMemcpyAsync(hkept.data(), kept.p, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+  AMB_CUDA(cudaStreamSynchronize(st));
+  check_status("pair coarse pseudo-inverse", AMB_EASSUMPTION);
+  int total = 0;
+  L.pair_rows.assign(np, {});
+  for (int p = 0; p < np; ++p) {
+    const PairTopo& P = tp.pairs[p];
+    const int64_t nfc = (int64_t)P.face.size();
+    const int64_t o = qp[(size_t)p * Q_NPAIRF + Q_OR];
+    std::vector<std::vector<double>> rr;
+    for (int l = 0; l < hkept[p]; ++l)
+      rr.emplace_back(hrows.begin() + o + l * nfc, hrows.begin() + o + (l + 1) * nfc);
+    PairReportH rep;
+    rep.level = lvl;
+    rep.s = P.s;
+    rep.t = P.t;
+    rep.n_computed = m;
+    rep.n_selected = nsel[p];
+    rep.n_rows = hkept[p];
+    rep.converged = conv[p];
+    rep.iterations = iters[p];
+    rep.lambda.assign(hl.begin() + (size_t)p * m, hl.begin() + (size_t)(p + 1) * m);
+    reports.push_back(rep);
+    total += hkept[p];
+    L.pair_rows[p] = rr;
+  }
+  for (int p = 0; p < np; ++p)
+    if (!L.pair_rows[p].empty()) add_adaptive_rows(tp, p, L.pair_rows[p]);
+  number_coarse(tp);
+  omega.push_back(om);
+  nadapt.push_back(total);
+}
+
+template void Engine<float>::adapt_level(LevelData<float>&);
+template void Engine<double>::adapt_level(LevelData<double>&);
+
+}  // namespace amb
