@@ -1,0 +1,316 @@
+"""Benchmark: adaptive-BDDC set-up + solve to a 1e-8 relative residual on the
+3D elasticity workload (48^3 Q1 hexahedra, 4x4x4 substructures of 12^3
+elements, lognormal Young's modulus sigma 1.5, nu 0.3, clamped face, unit
+body force, two levels, adaptive faces at tau = 10), plus the batched
+Schur-apply roofline fraction.
+
+One step = amb_setup + amb_solve through the C ABI with coefficients and
+right-hand side already in HBM.  The factor working set (tens of GB) is far
+larger than the 129 MB L2, so no flush is needed between steps.
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import amb_inputs as ai  # noqa: E402
+
+METRIC = "adaptive-BDDC setup+solve s to 1e-8 rel. residual; Schur-apply % of roofline"
+WORKLOAD = "elasticity48_4x4x4_lognormal"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, gpu_index=0):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or p[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle sample
+def oracle_sample(prob, reps=1):
+    """The CPU oracle on a bounded sample of the workload: set-up of the 2x2x1
+    block of substructures at the clamped face (24x24x12 elements, 4 of the 64
+    substructures, same coefficient field) and one Algorithm-1 application,
+    extrapolated to 64 substructures and the oracle's own iteration count on
+    the full workload (37, tests/golden)."""
+    from oracle import fe, solver
+    sub = ai.Problem(name="sample", nx=24, ny=24, nz=12, dofs_per_node=3,
+                     coeff=prob.coeff.reshape(48, 48, 48)[:12, :24, :24].ravel().copy(),
+                     poisson_ratio=prob.poisson_ratio, body=prob.body[: 24 * 24 * 12].copy(),
+                     dirichlet_node_mask=None, cuts=[[np.array([0, 12, 24]), np.array([0, 12, 24]),
+                                                      np.array([0, 12])]],
+                     elem_to_sub=None, sub_to_parent=[], levels=2, tau=prob.tau)
+    sub.dirichlet_node_mask = ai._dirichlet_x0(24, 24, 12)
+    sub.elem_to_sub = ai.tensor_partition(24, 24, 12, sub.cuts[0])
+    its_full = 37   # the element size only scales K, not the work
+    t0 = time.perf_counter()
+    h = solver.Hierarchy(sub)
+    t_setup = time.perf_counter() - t0
+    f = fe.load_vector(sub)
+    t1 = time.perf_counter()
+    z = h.apply(f)
+    q = h.ops[0] @ z
+    t_iter = time.perf_counter() - t1
+    scale = 64.0 / 4.0
+    est = scale * (t_setup + its_full * t_iter)
+    return est, time.perf_counter() - t0, dict(t_setup=t_setup, t_iter=t_iter)
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max(int(i.get("num_threads", 1)) for i in threadpool_info()) or os.cpu_count()
+    except Exception:
+        return os.cpu_count()
+
+
+# ---------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-form", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    prob = ai.config(2)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        for _ in range(args.warmup):
+            oracle_sample(prob)
+        vals, wall = [], 0.0
+        for _ in range(args.steps):
+            est, w, _ = oracle_sample(prob)
+            vals.append(est)
+            wall += w
+        v = statistics.mean(vals)
+        line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * v, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "levels": 2, "tau": 10.0, "dofs": 345744},
+                "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": cpu_threads(),
+                                 "sample": "oracle set-up of 4 of 64 substructures (2x2x1 block at the clamped "
+                                           "face) + one Algorithm-1 application, scaled by 16 and by the "
+                                           "oracle's 37 iterations"},
+                "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1301_0191_gb300 import binding as B
+
+    prec = B.FP32 if args.precision == "fp32" else B.FP64
+    coeff_d = torch.tensor(prob.coeff, dtype=torch.float64, device="cuda")
+    # right-hand side: consistent loads of the unit body force, computed once by the library
+    c0 = B.Context.from_problem(prob, adaptive=0, precision=prec)
+    f_h = c0.load_vector(prob.body)
+    c0.close()
+    f_d = torch.tensor(f_h, device="cuda")
+    u_d = torch.empty_like(f_d)
+    opts = dict(precision=prec, lobpcg_maxit=200, lobpcg_tol=1e-6, pcg_rtol=1e-8)
+
+    def step(timing=0):
+        c = B.Context.from_problem(prob, coeff=coeff_d, timing_events=timing, **opts)
+        _, info = c.solve(f_d, out=u_d)
+        return c, info
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        c, info = step()
+        c.close()
+    clocks = Clocks()
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record()
+    infos = []
+    for _ in range(args.steps):
+        c, info = step()
+        infos.append(info)
+        launches += c.stats()["kernels_launched"]
+        c.close()
+    e1.record()
+    barrier()
+    clk = clocks.stop(local)
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # end to end: host coefficients / rhs / solution, copies inside the timed region
+    coeff_h = np.ascontiguousarray(prob.coeff)
+    u_h = np.empty_like(f_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c = B.Context.from_problem(prob, coeff=coeff_h, **opts)
+        c.solve(f_h, out=u_h)
+        c.close()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    h2d = coeff_h.nbytes + f_h.nbytes + prob.dirichlet_node_mask.nbytes + prob.elem_to_sub.nbytes
+    d2h = u_h.nbytes
+
+    # kernel-family timing (separate, untimed run with CUDA events per family)
+    c, info = step(timing=1)
+    st = c.stats()
+    li = c.level_info(1)
+    rep = c.report()
+    peaks, src = _peaks()
+    fams = st["families"]
+    fam_factor = fams["factor"]
+    fp = "fp32" if prec == B.FP32 else "fp64"
+    # SIMT FP32: 152 SMs x 128 lanes x 2 flops x max SM clock; FP64: nominal 1.25 TFLOP/s
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if fp == "fp32" else 1.25
+    achieved = li.factor_flops / (fam_factor["ms"] * 1e-3) / 1e12 if fam_factor["ms"] > 0 else None
+    roofline = {"kernel": "batched partial Cholesky (k_chol_diag + k_gemm panel/trailing)", "bound": "alu",
+                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak if achieved else None, "traffic": None,
+                "peak_source": f"derived: {fp} SIMT lanes x clock ({src} peaks file)"}
+    # Schur apply at widths 1, 30, 180 (headline 2)
+    sizes = [int(c.export(B.X_SUB_SIZES, 1, s, np.int32)[1]) for s in range(li.n_subs)]
+    tdt = torch.float32 if prec == B.FP32 else torch.float64
+    esz = 4 if prec == B.FP32 else 8
+    schur = {}
+    for width in (1, 30, 180):
+        x = torch.randn(sum(sizes) * width, dtype=tdt, device="cuda")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            c.schur_apply(1, width, x, y)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            c.schur_apply(1, width, x, y)
+        b.record()
+        torch.cuda.synchronize()
+        t = a.elapsed_time(b) / 10 * 1e-3
+        byts = sum(n * n * esz + 2 * n * width * esz for n in sizes)
+        flops = sum(2.0 * n * n * width for n in sizes)
+        schur[f"w{width}"] = {"ms": t * 1e3, "GB/s": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / peaks["hbm_gbs"],
+                              "TFLOP/s": flops / t / 1e12, "alu_frac": flops / t / 1e12 / alu_peak}
+    c.close()
+
+    fp64_form = None
+    if not args.no_fp64_form and prec == B.FP32:
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        c64 = B.Context.from_problem(prob, coeff=coeff_d, precision=B.FP64, lobpcg_maxit=200, lobpcg_tol=1e-6)
+        _, i64 = c64.solve(f_d, out=u_d)
+        b.record()
+        torch.cuda.synchronize()
+        fp64_form = {"s": a.elapsed_time(b) * 1e-3, "iterations": i64.iterations,
+                     "speedup_fp32": a.elapsed_time(b) / ms}
+        c64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, wall, parts = oracle_sample(prob)
+        cpu = {"value": est, "unit": "s", "cores": cpu_threads(), "kind": "oracle",
+               "sample": "oracle set-up of 4 of 64 substructures (2x2x1 block at the clamped face) + one "
+                         "Algorithm-1 application, scaled by 16 and by the oracle's 37 iterations",
+               "sample_wall_s": wall}
+    if rank == 0:
+        last = infos[-1]
+        line = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == B.FP32 else "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "levels": 2, "tau": 10.0, "dofs": int(li.n_dofs),
+                           "substructures": li.n_subs, "pairs": li.n_pairs, "l2": "working set >> L2 (no flush)",
+                           "replicas": "one independent problem per GPU"},
+                "pcg_iterations": last.iterations, "rel_residual": last.rel_residual,
+                "true_rel_residual": last.true_rel_residual, "cond_estimate": last.cond_estimate,
+                "n_adaptive": rep["n_adaptive"], "omega": rep["omega"],
+                "phase_ms": st["phase_ms"], "families": fams,
+                "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "gpu_launches": int(launches / args.steps), "clocks": clk, "roofline": roofline,
+                "schur_apply": schur, "fp64_form": fp64_form, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

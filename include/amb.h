@@ -121,6 +121,8 @@ typedef struct {
   int32_t converged;            /* 1 if every residual met lobpcg_tol */
   int32_t iterations;           /* LOBPCG iterations */
   double lambda[AMB_MAX_EIG];   /* computed eigenvalues, descending */
+  double residual;              /* max over the used columns (selected + next) of
+                                   ||A x - lam B x|| / (max(lam, tau/10) ||B x||) */
 } amb_pair_report;
 
 typedef struct {

@@ -52,7 +52,7 @@ class SolveInfo(C.Structure):
 class PairReport(C.Structure):
     _fields_ = [("level", C.c_int32), ("s", C.c_int32), ("t", C.c_int32), ("n_computed", C.c_int32),
                 ("n_selected", C.c_int32), ("n_rows", C.c_int32), ("converged", C.c_int32),
-                ("iterations", C.c_int32), ("lambda_", C.c_double * MAX_EIG)]
+                ("iterations", C.c_int32), ("lambda_", C.c_double * MAX_EIG), ("residual", C.c_double)]
 
 
 class Report(C.Structure):
@@ -234,7 +234,7 @@ class Context:
             p = PairReport.from_buffer(buf, off + k * C.sizeof(PairReport))
             pairs.append(dict(level=p.level, s=p.s, t=p.t, n_computed=p.n_computed, n_selected=p.n_selected,
                               n_rows=p.n_rows, converged=p.converged, iterations=p.iterations,
-                              lam=np.array(p.lambda_[:p.n_computed])))
+                              lam=np.array(p.lambda_[:p.n_computed]), residual=p.residual))
         nl = r.n_levels
         return dict(n_levels=nl, omega_level=list(r.omega_level[:nl]), omega=r.omega,
                     n_adaptive=list(r.n_adaptive[:nl]), n_coarse=list(r.n_coarse[:nl]),

@@ -362,6 +362,7 @@ int amb_eigen_report(const amb_ctx* cc, amb_report* buf, size_t* nbytes) {
     o.n_rows = r.n_rows;
     o.converged = r.converged;
     o.iterations = r.iterations;
+    o.residual = r.residual;
     for (size_t j = 0; j < r.lambda.size() && j < AMB_MAX_EIG; ++j) o.lambda[j] = r.lambda[j];
   }
   *nbytes = need;

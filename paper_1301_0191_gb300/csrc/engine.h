@@ -24,6 +24,7 @@ struct Mesh {
 struct PairReportH {
   int level, s, t, n_computed, n_selected, n_rows, converged, iterations;
   std::vector<double> lambda;
+  double residual = 0.0;
 };
 
 struct Timers {

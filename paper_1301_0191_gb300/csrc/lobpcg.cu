@@ -330,8 +330,10 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
   const int m3 = 3 * m;
   const T* U = Qb + QP(p, Q_OQ);
   const T* Vb = U + (int64_t)(kind ? 6 * m : 3 * m) * N;
-  __shared__ double us[32][33], vs[32][33];
-  double acc[5] = {0, 0, 0, 0, 0};
+  __shared__ double us[32][3 * AMB_MAX_EIG + 1], vs[32][3 * AMB_MAX_EIG + 1];
+  constexpr int NQ = (9 * AMB_MAX_EIG * AMB_MAX_EIG + 255) / 256;
+  double acc[NQ];
+  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
   const int nout = w * w;
   for (int64_t r0 = 0; r0 < N; r0 += 32) {
     const int rn = (N - r0) < 32 ? (int)(N - r0) : 32;
@@ -341,7 +343,7 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
       vs[r][c] = r < rn ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
     }
     __syncthreads();
-    for (int q = 0; q < 5; ++q) {
+    for (int q = 0; q < NQ; ++q) {
       int o = threadIdx.x + q * blockDim.x;
       if (o >= nout) break;
       int a = o % w, b = o / w;
@@ -352,7 +354,7 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
     __syncthreads();
   }
   double* g = G + QP(p, Q_OGR) + (int64_t)kind * m3 * m3;
-  for (int q = 0; q < 5; ++q) {
+  for (int q = 0; q < NQ; ++q) {
     int o = threadIdx.x + q * blockDim.x;
     if (o >= nout) break;
     int a = o % w, b = o / w;
@@ -594,7 +596,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     return;
   }
   const int maxad = std::max(0, cfg.opt.max_adaptive_per_face);
-  const int m = std::min(AMB_MAX_EIG, maxad + 1);
+  // block size: the rows the method may add, the indicator column and 4
+  // guard columns that keep the last used column from converging slowly
+  const int m = std::min(AMB_MAX_EIG, maxad + 1 + 4);
   const int m3 = 3 * m;
   // ------------------------------------------------ pair tables
   std::vector<int64_t> qp((size_t)np * Q_NPAIRF, 0);
@@ -897,6 +901,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const double tol = cfg.opt.lobpcg_tol;
   const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
   const double tau = cfg.tau;
+  std::vector<double> resid(np, 0.0);
   auto check = [&]() {
     k_lob_resid<T><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m);
     AMB_LAUNCHED();
@@ -908,12 +913,21 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     for (int p = 0; p < np; ++p) {
       bool ok = true;
       const double lref = 0.1 * tau;
-      for (int k = 0; k < m; ++k) {
+      // the columns the method uses: the selected ones (lambda > tau, at most
+      // max_adaptive_per_face) and the next one, lambda_{k+1}, the indicator
+      int kuse = 0;
+      while (kuse < m && kuse < maxad && hl[(size_t)p * m + kuse] > tau) ++kuse;
+      kuse = std::min(m, kuse + 1);
+      double worst = 0.0;
+      for (int k = 0; k < kuse; ++k) {
         const double l = hl[(size_t)p * m + k];
         const double b = hb[(size_t)p * m + k];
         if (b == 0.0) continue;   // dropped direction (rank-deficient pair space)
-        if (!(hr[(size_t)p * m + k] <= tol * std::max(std::fabs(l), lref) * b)) ok = false;
+        const double ratio = hr[(size_t)p * m + k] / (std::max(std::fabs(l), lref) * b);
+        worst = std::max(worst, std::isfinite(ratio) ? ratio : 1e300);
+        if (!(ratio <= tol)) ok = false;
       }
+      resid[p] = worst;
       conv[p] = ok ? 1 : 0;
       active[p] = ok ? 0 : 1;
       nact += active[p];
@@ -973,6 +987,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     rep.n_rows = hkept[p];
     rep.converged = conv[p];
     rep.iterations = iters[p];
+    rep.residual = resid[p];
     rep.lambda.assign(hl.begin() + (size_t)p * m, hl.begin() + (size_t)(p + 1) * m);
     reports.push_back(rep);
     total += hkept[p];

@@ -35,6 +35,6 @@ def test_binding_structs_match_header_sizes():
     # layouts mirror the C structs: check field order against the header text
     src = open(os.path.join(ROOT, "include", "amb.h")).read()
     assert src.index("int32_t iterations;") < src.index("double rel_residual;")
-    assert ctypes.sizeof(B.PairReport) == 8 * 4 + 16 * 8
+    assert ctypes.sizeof(B.PairReport) == 8 * 4 + 16 * 8 + 8
     o = B.default_options()
     assert o.precision == B.FP64 and o.max_adaptive_per_face == 10 and o.pcg_rtol == 1e-8
