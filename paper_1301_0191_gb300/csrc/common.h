@@ -138,10 +138,12 @@ enum GemmFlags : int {
   G_OUT_LOWER = 64,    // write only C(i,j) with i >= j
 };
 
-// Batched product driver (dense.cu).
-template <typename T>
+// Batched product driver (dense.cu).  A may be stored in a narrower type
+// TA than the compute/accumulate type T (e.g. FP32 Schur complements times
+// FP64 block vectors with FP64 accumulation).
+template <typename T, typename TA = T>
 void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
-                  T alpha, T beta, const T* A, const T* B, T* C);
+                  T alpha, T beta, const TA* A, const T* B, T* C);
 
 // Gather/scatter descriptor for batched matrix-vector work (dense.cu).
 struct GemvDesc {

@@ -20,21 +20,21 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float4; static constexpr int W = 4; };
 template <> struct Vec2<double> { using type = double2; static constexpr int W = 2; };
 
-template <typename T>
+template <typename T, typename TA>
 struct GemmArgs {
   const GemmDesc* desc;
   const int* prefix;   // ndesc+1 tile prefix sums
   int ndesc;
   int flags;
   T alpha, beta;
-  const T* A;
+  const TA* A;
   const T* B;
   T* C;
 };
 
-template <typename T, int BM, int BN, int BK, int TM, int TN>
+template <typename T, typename TA, int BM, int BN, int BK, int TM, int TN>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_gemm(GemmArgs<T> g) {
+k_gemm(GemmArgs<T, TA> g) {
   constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
   constexpr int PAD = 16 / sizeof(T);
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
@@ -61,7 +61,7 @@ k_gemm(GemmArgs<T> g) {
   if (fl & G_TRI_A_UPPER) kbeg = max(kbeg, (i0 / BK) * BK);
   if (fl & G_TRI_B_LOWER) kbeg = max(kbeg, (j0 / BK) * BK);
 
-  const T* A = g.A + d.a;   // may alias C (in-place panel update)
+  const TA* A = g.A + d.a;   // may alias C (in-place panel update)
   const T* __restrict__ B = g.B + d.b;
   const bool ta = fl & G_TRANS_A, tb = fl & G_TRANS_B;
   const int tid = threadIdx.x;
@@ -79,7 +79,7 @@ k_gemm(GemmArgs<T> g) {
       if ((fl & G_TRI_A_LOWER) && gk > gi) ok = false;
       if ((fl & G_TRI_A_UPPER) && gk < gi) ok = false;
       T v = T(0);
-      if (ok) v = ta ? A[gk + (int64_t)gi * d.lda] : A[gi + (int64_t)gk * d.lda];
+      if (ok) v = (T)(ta ? A[gk + (int64_t)gi * d.lda] : A[gi + (int64_t)gk * d.lda]);
       ra[q] = v;
     }
 #pragma unroll
@@ -177,9 +177,9 @@ template <typename T> struct GemmTile;
 template <> struct GemmTile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
 
-template <typename T>
+template <typename T, typename TA>
 void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
-                  T alpha, T beta, const T* A, const T* B, T* C) {
+                  T alpha, T beta, const TA* A, const T* B, T* C) {
   using TL = GemmTile<T>;
   std::vector<GemmDesc> dd;
   std::vector<int> prefix;
@@ -200,7 +200,7 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   memcpy(blob.data(), dd.data(), dd.size() * sizeof(GemmDesc));
   memcpy(blob.data() + dd.size() * sizeof(GemmDesc), prefix.data(), prefix.size() * sizeof(int));
   char* dev = static_cast<char*>(ring.push(blob.data(), blob.size(), st));
-  GemmArgs<T> g;
+  GemmArgs<T, TA> g;
   g.desc = reinterpret_cast<const GemmDesc*>(dev);
   g.prefix = reinterpret_cast<const int*>(dev + dd.size() * sizeof(GemmDesc));
   g.ndesc = (int)dd.size();
@@ -211,14 +211,16 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   g.B = B;
   g.C = C;
   constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
-  k_gemm<T, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
+  k_gemm<T, TA, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
   AMB_LAUNCHED();
 }
 
-template void gemm_batched<float>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, float, float,
-                                  const float*, const float*, float*);
-template void gemm_batched<double>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, double, double,
-                                   const double*, const double*, double*);
+template void gemm_batched<float, float>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, float, float,
+                                         const float*, const float*, float*);
+template void gemm_batched<double, double>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, double,
+                                           double, const double*, const double*, double*);
+template void gemm_batched<double, float>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, double,
+                                          double, const float*, const double*, double*);
 
 // ------------------------------------------------------------------ GEMV
 // y = alpha op(A) x + beta y, one vector per descriptor.  No-transpose:

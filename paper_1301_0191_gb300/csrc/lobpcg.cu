@@ -28,7 +28,7 @@ namespace {
 
 enum PairField {
   Q_S, Q_T, Q_NS, Q_NT, Q_N, Q_NF, Q_OQ, Q_OT, Q_OJ, Q_OF, Q_FOFF, Q_GBEG, Q_GEND, Q_FACEOFF, Q_FACEN,
-  Q_CMS, Q_CMT, Q_NCP, Q_NCS, Q_NCT, Q_OC, Q_OPI, Q_OGR, Q_OCC, Q_OR, Q_NPAIRF
+  Q_CMS, Q_CMT, Q_NCP, Q_NCS, Q_NCT, Q_OC, Q_OPI, Q_OGR, Q_OCC, Q_OR, Q_OO, Q_NPAIRF
 };
 #define QP(p, f) qp[(int64_t)(p) * Q_NPAIRF + (f)]
 
@@ -168,7 +168,7 @@ __global__ void k_lob_random(T* Qb, const int64_t* qp, int m, uint64_t seed) {
 // offset QP(p, which) (+ c0*N).  One warp per (group, column).
 template <typename T>
 __global__ void k_lob_project(T* base, const int64_t* qp, int which, int c0, int w, const int32_t* goff,
-                              const int32_t* gent, const T* gw, const int32_t* ps, const int32_t* pt) {
+                              const int32_t* gent, const double* gw, const int32_t* ps, const int32_t* pt) {
   const int p = blockIdx.x;
   const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS);
   const int64_t g0 = QP(p, Q_GBEG), g1 = QP(p, Q_GEND), foff = QP(p, Q_FOFF);
@@ -199,37 +199,49 @@ __global__ void k_lob_project(T* base, const int64_t* qp, int which, int c0, int
   }
 }
 
-// J_s = d_t * j, J_t = -d_s * j with j = v^s_f - v^t_f (nf x w each)
-template <typename T>
-__global__ void k_lob_jump(T* J, const T* base, const int64_t* qp, int which, int c0, int w, const int32_t* ps,
-                           const int32_t* pt, const T* ws, const T* wt) {
+// J_s = d_t * j, J_t = -d_s * j with j = v^s_f - v^t_f (nf x w each).  The
+// block vectors (V) are FP64; J is in the operator precision T.
+template <typename T, typename V>
+__global__ void k_lob_jump(T* J, const V* base, const int64_t* qp, int which, int c0, int w, const int32_t* ps,
+                           const int32_t* pt, const double* ws, const double* wt) {
   const int p = blockIdx.y;
   const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS), nf = QP(p, Q_NF), foff = QP(p, Q_FOFF);
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nf * w) return;
   const int64_t f = idx % nf, col = idx / nf;
-  const T* v = base + QP(p, which) + (c0 + col) * N;
-  const T j = v[ps[foff + f]] - v[ns + pt[foff + f]];
+  const V* v = base + QP(p, which) + (c0 + col) * N;
+  const double j = (double)v[ps[foff + f]] - (double)v[ns + pt[foff + f]];
   T* Jb = J + QP(p, Q_OJ);
-  Jb[f + col * nf] = wt[foff + f] * j;
-  Jb[nf * w + f + col * nf] = -ws[foff + f] * j;
+  Jb[f + col * nf] = (T)(wt[foff + f] * j);
+  Jb[nf * w + f + col * nf] = (T)(-ws[foff + f] * j);
 }
 
 // out = (I - E)^T [Y_s ; Y_t] scattered on f (s copy x, t copy -x), zero elsewhere
-template <typename T>
-__global__ void k_lob_iet(T* base, const int64_t* qp, int which, int c0, const T* J, int w, const int32_t* ps,
-                          const int32_t* pt, const T* ws, const T* wt) {
+template <typename T, typename V>
+__global__ void k_lob_iet(V* base, const int64_t* qp, int which, int c0, const T* J, int w, const int32_t* ps,
+                          const int32_t* pt, const double* ws, const double* wt) {
   const int p = blockIdx.x, col = blockIdx.y;
   const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS), nf = QP(p, Q_NF), foff = QP(p, Q_FOFF);
-  T* v = base + QP(p, which) + (int64_t)(c0 + col) * N;
-  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) v[i] = T(0);
+  V* v = base + QP(p, which) + (int64_t)(c0 + col) * N;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) v[i] = V(0);
   __syncthreads();
   const T* Y = J + QP(p, Q_OJ) + 2 * nf * w;
   for (int64_t f = threadIdx.x; f < nf; f += blockDim.x) {
-    const T x = wt[foff + f] * Y[f + col * nf] - ws[foff + f] * Y[nf * w + f + col * nf];
-    v[ps[foff + f]] = x;
-    v[ns + pt[foff + f]] = -x;
+    const double x = wt[foff + f] * (double)Y[f + col * nf] - ws[foff + f] * (double)Y[nf * w + f + col * nf];
+    v[ps[foff + f]] = (V)x;
+    v[ns + pt[foff + f]] = (V)(-x);
   }
+}
+
+// copy an N x w column block between the FP64 block vectors and the
+// operator-precision staging blocks (per pair offsets QP(p, wd), QP(p, ws))
+template <typename To, typename Ti>
+__global__ void k_lob_convert(To* dst, const Ti* src, const int64_t* qp, int wd, int cd, int wsrc, int cs, int w) {
+  const int p = blockIdx.y;
+  const int64_t N = QP(p, Q_N);
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N * w) return;
+  dst[QP(p, wd) + cd * N + idx] = (To)src[QP(p, wsrc) + cs * N + idx];
 }
 
 template <typename T>
@@ -324,8 +336,9 @@ __global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const 
 // FP64 Gram matrices G = U^T V over the first w columns of the panel;
 // kind 0: V = A-block, kind 1: V = B-block.
 template <typename T>
-__global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int w) {
+__global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int w, const int* act) {
   const int p = blockIdx.x, kind = blockIdx.y;
+  if (!act[p]) return;
   const int64_t N = QP(p, Q_N);
   const int m3 = 3 * m;
   const T* U = Qb + QP(p, Q_OQ);
@@ -366,7 +379,8 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
 // reduced standard eigenproblem; coefficients Cc = [Cx | Cp] (3m x 2m, T)
 // and the m largest Ritz values.  Frozen pairs keep X (Cx = I, Cp = 0).
 template <typename T>
-__global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w) {
+__global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w,
+                         double drop) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
   const int m3 = 3 * m;
@@ -416,7 +430,7 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   if (threadIdx.x == 0) {
     double smax = GB[ord[0] + ord[0] * w];
     int r = 0;
-    while (r < w && GB[ord[r] + ord[r] * w] > 1e-10 * smax && smax > 0.0) ++r;
+    while (r < w && GB[ord[r] + ord[r] * w] > drop * smax && smax > 0.0) ++r;
     rank_sh = r;
   }
   __syncthreads();
@@ -475,8 +489,10 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
 
 // R = A X - B X diag(lambda) into the W slot; residual and B-norms per column
 template <typename T>
-__global__ void k_lob_resid(T* Qb, double* rn, double* bn, const double* lam, const int64_t* qp, int m) {
+__global__ void k_lob_resid(T* Qb, double* rn, double* bn, const double* lam, const int64_t* qp, int m,
+                            const int* act) {
   const int p = blockIdx.x, col = blockIdx.y;
+  if (!act[p]) return;
   const int64_t N = QP(p, Q_N);
   T* base = Qb + QP(p, Q_OQ);
   const T* AX = base + (int64_t)(3 * m + col) * N;
@@ -501,8 +517,9 @@ __global__ void k_lob_resid(T* Qb, double* rn, double* bn, const double* lam, co
 
 // copy the updated blocks back: Tp = [Xn Pn | AXn APn | BXn BPn] -> panel
 template <typename T>
-__global__ void k_lob_copyback(T* Qb, const T* Tp, const int64_t* qp, int m) {
+__global__ void k_lob_copyback(T* Qb, const T* Tp, const int64_t* qp, int m, const int* act) {
   const int p = blockIdx.y;
+  if (!act[p]) return;
   const int64_t N = QP(p, Q_N);
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * 6 * m) return;
@@ -570,8 +587,9 @@ __global__ void k_lob_rows(double* rows, int* kept, const T* Qb, const int64_t* 
 }
 
 template <typename T>
-__global__ void k_lob_copy_w(T* Tp, const T* Qb, const int64_t* qp, int m) {
+__global__ void k_lob_copy_w(T* Tp, const T* Qb, const int64_t* qp, int m, const int* act) {
   const int p = blockIdx.y;
+  if (!act[p]) return;
   const int64_t N = QP(p, Q_N);
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * m) return;
@@ -600,6 +618,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   // guard columns that keep the last used column from converging slowly
   const int m = std::min(AMB_MAX_EIG, maxad + 1 + 4);
   const int m3 = 3 * m;
+  // SVQB: directions whose scaled B-Gram eigenvalue is below drop * max are
+  // numerically dependent at the storage precision and are discarded
+  const double svqb_drop = sizeof(T) == 4 ? 1e-5 : 1e-10;
   // ------------------------------------------------ pair tables
   std::vector<int64_t> qp((size_t)np * Q_NPAIRF, 0);
   std::vector<int32_t> hps, hpt, hgoff(1, 0), hgent, hface, hcms, hcmt;
@@ -677,32 +698,42 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   }
   AMB_CHECK(max_ncp <= kJacobiMax, AMB_EINVAL,
             "pair coarse space larger than " + std::to_string(kJacobiMax) + " dofs");
+  // operator staging blocks (N x m in the factor precision)
+  int64_t oO = 0;
+  for (int p = 0; p < np; ++p) {
+    qp[(size_t)p * Q_NPAIRF + Q_OO] = oO;
+    oO += qp[(size_t)p * Q_NPAIRF + Q_N] * m;
+  }
   DevBuf dqp, dps, dpt, dws, dwt, dgoff, dgent, dgw, dface, dcms, dcmt, dacs, dact;
   upload(dqp, qp, st);
   upload(dps, hps, st);
   upload(dpt, hpt, st);
-  std::vector<T> tws(hws.begin(), hws.end()), twt(hwt.begin(), hwt.end()), tgw(hgw.begin(), hgw.end());
-  upload(dws, tws, st);
-  upload(dwt, twt, st);
+  upload(dws, hws, st);
+  upload(dwt, hwt, st);
   upload(dgoff, hgoff, st);
   upload(dgent, hgent, st);
-  upload(dgw, tgw, st);
+  upload(dgw, hgw, st);
   upload(dface, hface, st);
   upload(dcms, hcms, st);
   upload(dcmt, hcmt, st);
   upload(dacs, acs, st);
   upload(dact, act, st);
-  DevBuf Qb, Tp, Jb, Sff, Zb, Qc, Cb, Pinv, Gr, Cc, lam, rn, bn, act_d, rows, kept, nsel_d;
-  Qb.alloc(oQ * sizeof(T));
-  Tp.alloc(oT * sizeof(T));
-  Jb.alloc(oJ * sizeof(T));
+  // Block vectors, their operator images and the Rayleigh-Ritz coefficients
+  // are FP64 (V); only the operator products run in the factor precision T.
+  using V = double;
+  DevBuf Qb, Tp, Jb, Sff, Zb, Qc, Cb, Pinv, Gr, Cc, lam, rn, bn, act_d, rows, kept, nsel_d, Oin, Oout;
+  Qb.alloc(oQ * sizeof(V));
+  Tp.alloc(oT * sizeof(V));
+  Oin.alloc(oO * sizeof(T));
+  Oout.alloc(oO * sizeof(T));
+  Jb.alloc(oJ * sizeof(V));
   Sff.alloc(oF * sizeof(T));
   Zb.alloc(oZ * sizeof(T));
   Qc.alloc(oQc * sizeof(T));
   Cb.alloc(oC * sizeof(T));
   Pinv.alloc(oPi * sizeof(T));
   Gr.alloc(oGr * sizeof(double));
-  Cc.alloc(oCc * sizeof(T));
+  Cc.alloc(oCc * sizeof(V));
   lam.alloc((size_t)np * m * sizeof(double));
   rn.alloc((size_t)np * m * sizeof(double));
   bn.alloc((size_t)np * m * sizeof(double));
@@ -712,8 +743,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   nsel_d.alloc(np * sizeof(int));
   AMB_CUDA(cudaMemsetAsync(Gr.p, 0, oGr * sizeof(double), st));
   const int64_t* QPd = dptr<int64_t>(dqp);
-  T* Q = dptr<T>(Qb);
+  V* Q = dptr<V>(Qb);
   const T one = T(1), zero = T(0);
+  std::vector<int> active(np, 1), iters(np, 0), conv(np, 0);
 
   // S_ff of each side (gathered once)
   {
@@ -750,9 +782,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
 
   // ------------------------------------------------ operators on panel column blocks
   // slot indices (column offsets in units of m): X 0, W 1, P 2, AX 3, AW 4, AP 5, BX 6, BW 7, BP 8
-  auto project = [&](T* base, int which, int c0, int w) {
-    k_lob_project<T><<<np, 256, 0, st>>>(base, QPd, which, c0, w, dptr<int32_t>(dgoff), dptr<int32_t>(dgent),
-                                         dptr<T>(dgw), dptr<int32_t>(dps), dptr<int32_t>(dpt));
+  auto project = [&](V* base, int which, int c0, int w) {
+    k_lob_project<V><<<np, 256, 0, st>>>(base, QPd, which, c0, w, dptr<int32_t>(dgoff), dptr<int32_t>(dgent),
+                                         dptr<double>(dgw), dptr<int32_t>(dps), dptr<int32_t>(dpt));
     AMB_LAUNCHED();
   };
   int64_t maxN = 0, maxnf = 0;
@@ -764,49 +796,65 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     k_lob_zero<T><<<dim3(nblk(maxN * w), np), 256, 0, st>>>(base, QPd, which, c0, w);
     AMB_LAUNCHED();
   };
+  // FP64 block -> operator staging block, and back
+  auto to_op = [&](const V* src, int which, int c0) {
+    k_lob_convert<T, V><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<T>(Oin), src, QPd, Q_OO, 0, which, c0, m);
+    AMB_LAUNCHED();
+  };
+  auto from_op = [&](int cout) {
+    k_lob_convert<V, T><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(Q, dptr<T>(Oout), QPd, Q_OQ, cout * m, Q_OO, 0, m);
+    AMB_LAUNCHED();
+  };
   // out slot = A * (in slot); in and out are column blocks of the panel
   auto applyA = [&](int cin, int cout) {
-    k_lob_jump<T><<<dim3(nblk(maxnf * m), np), 256, 0, st>>>(dptr<T>(Jb), Q, QPd, Q_OQ, cin * m, m, dptr<int32_t>(dps),
-                                                             dptr<int32_t>(dpt), dptr<T>(dws), dptr<T>(dwt));
+    k_lob_jump<V, V><<<dim3(nblk(maxnf * m), np), 256, 0, st>>>(dptr<V>(Jb), Q, QPd, Q_OQ, cin * m, m,
+                                                                dptr<int32_t>(dps), dptr<int32_t>(dpt),
+                                                                dptr<double>(dws), dptr<double>(dwt));
     AMB_LAUNCHED();
     std::vector<GemmDesc> d;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
       const int nf = (int)q[Q_NF];
       for (int side = 0; side < 2; ++side)
         d.push_back(GemmDesc{nf, m, nf, std::max(nf, 1), std::max(nf, 1), std::max(nf, 1),
                              q[Q_OF] + side * (int64_t)nf * nf, q[Q_OJ] + side * (int64_t)nf * m,
                              q[Q_OJ] + (2 + side) * (int64_t)nf * m});
     }
-    gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(Sff), dptr<T>(Jb), dptr<T>(Jb));
-    k_lob_iet<T><<<dim3(np, m), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, dptr<T>(Jb), m, dptr<int32_t>(dps),
-                                             dptr<int32_t>(dpt), dptr<T>(dws), dptr<T>(dwt));
+    gemm_batched<V, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(Sff), dptr<V>(Jb), dptr<V>(Jb));
+    k_lob_iet<V, V><<<dim3(np, m), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, dptr<V>(Jb), m, dptr<int32_t>(dps),
+                                                dptr<int32_t>(dpt), dptr<double>(dws), dptr<double>(dwt));
     AMB_LAUNCHED();
     project(Q, Q_OQ, cout * m, m);
   };
   auto applyB = [&](int cin, int cout) {
+    // FP32 operator entries, FP64 block vectors and accumulation
     std::vector<GemmDesc> d;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
       const int64_t N = q[Q_N];
       for (int side = 0; side < 2; ++side) {
         const int sub = (int)(side ? q[Q_T] : q[Q_S]);
         const int ng = L.ng[sub];
         const int64_t r0 = side ? q[Q_NS] : 0;
-        d.push_back(GemmDesc{ng, m, ng, std::max(ng, 1), (int)N, (int)N, L.pS.off[sub],
-                             q[Q_OQ] + cin * m * N + r0, q[Q_OQ] + cout * m * N + r0});
+        d.push_back(GemmDesc{ng, m, ng, std::max(ng, 1), (int)N, (int)N, L.pS.off[sub], q[Q_OQ] + cin * m * N + r0,
+                             q[Q_OQ] + cout * m * N + r0});
       }
     }
-    gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(L.S), Q, Q);
+    gemm_batched<V, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+    
     project(Q, Q_OQ, cout * m, m);
   };
   // W slot = M * (R in the temp panel, columns 0..m)
   auto applyM = [&](int cout) {
-    project(dptr<T>(Tp), Q_OT, 0, m);
-    zero_block(Q, Q_OQ, cout * m, m);
+    project(dptr<V>(Tp), Q_OT, 0, m);
+    to_op(dptr<V>(Tp), Q_OT, 0);
+    zero_block(dptr<T>(Oout), Q_OO, 0, m);
     std::vector<GemmDesc> d1, d2, d3, d4, d5, dc1, dc2, dpi;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
       const int64_t N = q[Q_N];
       int64_t zo = zoff[p], qo = qcoff[p];
       int64_t co = q[Q_OC];
@@ -814,7 +862,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
         const int sub = (int)(side ? q[Q_T] : q[Q_S]);
         const int nd = L.nd[sub], ncp = L.ncp[sub], nc = L.nc[sub], ng = L.ng[sub];
         const int64_t r0 = side ? q[Q_NS] : 0;
-        const int64_t rin = q[Q_OT] + r0, rout = q[Q_OQ] + cout * m * N + r0;
+        const int64_t rin = q[Q_OO] + r0, rout = q[Q_OO] + r0;
         const int ldd = std::max(nd, 1), ldc = std::max(ncp, 1);
         // Neumann: z = L_D^{-1} r_D; qv = Y^T z; l = Ginv qv; z -= Y l; out_D = L_D^{-T} z
         d1.push_back(GemmDesc{nd, m, nd, ldd, (int)N, ldd, L.pLD.off[sub], rin, zo});
@@ -830,16 +878,18 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       }
     }
     // the S-side and T-side blocks share base pointers: Zb for z, Qc for q/l, Cb for coarse
-    gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Tp), dptr<T>(Zb));
+    gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Oin), dptr<T>(Zb));
     gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
     gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
     gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
-    gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), Q);
-    gemm_batched<T>(st, ring, dc1, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(Tp), dptr<T>(Cb));
+    gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb),
+                    dptr<T>(Oout));
+    gemm_batched<T>(st, ring, dc1, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(Oin), dptr<T>(Cb));
     k_lob_cgather<T><<<np, 256, 0, st>>>(dptr<T>(Cb), QPd, m, dptr<int32_t>(dcms), dptr<int32_t>(dcmt));
     AMB_LAUNCHED();
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
       const int ncpr = (int)q[Q_NCP];
       const int64_t cp = q[Q_OC] + (q[Q_NCS] + q[Q_NCT]) * m;
       dpi.push_back(GemmDesc{ncpr, m, ncpr, std::max(ncpr, 1), std::max(ncpr, 1), std::max(ncpr, 1), q[Q_OPI], cp,
@@ -850,6 +900,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     AMB_LAUNCHED();
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
       const int64_t N = q[Q_N];
       const int64_t us = q[Q_OC] + (q[Q_NCS] + q[Q_NCT] + 2 * q[Q_NCP]) * m;
       int64_t uo = us;
@@ -858,19 +909,21 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
         const int nc = L.nc[sub], ng = L.ng[sub];
         const int64_t r0 = side ? q[Q_NS] : 0;
         dc2.push_back(GemmDesc{ng, m, nc, std::max(ng, 1), std::max(nc, 1), (int)N, L.pPsi.off[sub], uo,
-                               q[Q_OQ] + cout * m * N + r0});
+                               q[Q_OO] + r0});
         uo += (int64_t)nc * m;
       }
     }
-    gemm_batched<T>(st, ring, dc2, 0, one, one, dptr<T>(L.Psi), dptr<T>(Cb), Q);
+    gemm_batched<T>(st, ring, dc2, 0, one, one, dptr<T>(L.Psi), dptr<T>(Cb), dptr<T>(Oout));
+    from_op(cout);
     project(Q, Q_OQ, cout * m, m);
   };
   auto rayleigh_ritz = [&](int w) {
-    k_lob_gram<T><<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), Q, QPd, m, w);
+    k_lob_gram<V><<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), Q, QPd, m, w, dptr<int>(act_d));
     AMB_LAUNCHED();
     const size_t smem = (size_t)(5 * w * w + w) * sizeof(double);
-    AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lob_rr<T><<<np, 256, smem, st>>>(dptr<T>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w);
+    AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_lob_rr<V><<<np, 256, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
+                                       svqb_drop);
     AMB_LAUNCHED();
     // [Xn Pn] = U Cc, [AXn APn] = AU Cc, [BXn BPn] = BU Cc
     std::vector<GemmDesc> d;
@@ -878,32 +931,34 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       d.clear();
       for (int p = 0; p < np; ++p) {
         const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+        if (!active[p]) continue;
         const int64_t N = q[Q_N];
         d.push_back(GemmDesc{(int)N, 2 * m, w, (int)N, m3, (int)N, q[Q_OQ] + (int64_t)3 * g * m * N, q[Q_OCC],
                              q[Q_OT] + (int64_t)2 * g * m * N});
       }
-      gemm_batched<T>(st, ring, d, 0, one, zero, Q, dptr<T>(Cc), dptr<T>(Tp));
+      gemm_batched<V>(st, ring, d, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     }
-    k_lob_copyback<T><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<T>(Tp), QPd, m);
+    k_lob_copyback<V><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<V>(Tp), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
   };
 
   // ------------------------------------------------ LOBPCG
-  k_lob_random<T><<<dim3(nblk(maxN * 9 * m), np), 256, 0, st>>>(Q, QPd, m, cfg.opt.seed + 7919ull * lvl);
+  k_lob_random<V><<<dim3(nblk(maxN * 9 * m), np), 256, 0, st>>>(Q, QPd, m, cfg.opt.seed + 7919ull * lvl);
   AMB_LAUNCHED();
-  std::vector<int> active(np, 1), iters(np, 0), conv(np, 0);
   AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
   project(Q, Q_OQ, 0, m);
   applyA(0, 3);
   applyB(0, 6);
   rayleigh_ritz(m);
   std::vector<double> hl((size_t)np * m), hr((size_t)np * m), hb((size_t)np * m);
-  const double tol = cfg.opt.lobpcg_tol;
+  // Residuals of FP32 block vectors cannot fall far below sqrt(eps_32); the
+  // residual target is clamped to what the storage precision can reach.
+  const double tol = sizeof(T) == 4 ? std::max(cfg.opt.lobpcg_tol, 1e-4) : cfg.opt.lobpcg_tol;
   const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
   const double tau = cfg.tau;
   std::vector<double> resid(np, 0.0);
   auto check = [&]() {
-    k_lob_resid<T><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m);
+    k_lob_resid<V><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
     AMB_CUDA(cudaMemcpyAsync(hl.data(), lam.p, hl.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
     AMB_CUDA(cudaMemcpyAsync(hr.data(), rn.p, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -941,7 +996,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     for (int p = 0; p < np; ++p) iters[p] += active[p];
     AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     // R (W slot) -> temp panel columns 0..m, then W = M R
-    k_lob_copy_w<T><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<T>(Tp), Q, QPd, m);
+    k_lob_copy_w<V><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<V>(Tp), Q, QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
     applyM(1);
     applyA(1, 4);
@@ -960,7 +1015,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     om = std::max(om, next);
   }
   AMB_CUDA(cudaMemcpyAsync(nsel_d.p, nsel.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-  k_lob_rows<T><<<np, 256, 0, st>>>(dptr<double>(rows), dptr<int>(kept), Q, QPd, dptr<int>(nsel_d), dptr<int32_t>(dps),
+  k_lob_rows<V><<<np, 256, 0, st>>>(dptr<double>(rows), dptr<int>(kept), Q, QPd, dptr<int>(nsel_d), dptr<int32_t>(dps),
                                     dptr<int32_t>(dface), m);
   AMB_LAUNCHED();
   std::vector<double> hrows(std::max<int64_t>(oR, 1));
