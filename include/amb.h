@@ -206,6 +206,25 @@ int amb_grad(amb_ctx* ctx, int32_t qoi_kind, const double* dq_du, double* grad_l
  * AMB_X_SUB_DOFS).  Y must not overlap X. */
 int amb_schur_apply(amb_ctx* ctx, int32_t level, int32_t width, const void* x, void* y);
 
+/* amb_schur_apply for callers that cannot allocate device memory during the
+ * call: processes whose device memory is held by their own pool (a caching
+ * allocator that owns the GPU) or that cannot afford the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  The paper has no counterpart;
+ * this is an interface variant of the batched Schur apply.
+ *
+ * Same arguments, result and layout as amb_schur_apply.  The launch
+ * descriptors are staged in a fixed 64 KiB device array that is part of the
+ * library image (present on every GPU that loads the library until the
+ * process exits); the call performs no cudaMalloc, cudaFree or other
+ * allocating call.  Limits: at most 1024 substructures on the level, else
+ * AMB_EINVAL with a message.  The context's device must be current.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's descriptors:
+ * calls whose GPU work overlaps (other streams, other host threads) race on
+ * it, so serialise them.  Returns after the context stream has finished. */
+int amb_schur_apply_noalloc(amb_ctx* ctx, int32_t level, int32_t width, const void* x, void* y);
+
 /* Level sizes for callers that size buffers or compare with a reference. */
 typedef struct {
   int32_t n_subs, n_pairs, n_corner_nodes, n_edges, n_faces;

@@ -93,6 +93,8 @@ def lib():
         L.amb_eigen_report.argtypes = [vp, vp, sz]
         L.amb_grad.argtypes = [vp, i32, vp, vp]
         L.amb_schur_apply.argtypes = [vp, i32, i32, vp, vp]
+        L.amb_schur_apply_noalloc.argtypes = [vp, i32, i32, vp, vp]
+        L.amb_schur_apply_noalloc.restype = C.c_int
         L.amb_level_info.argtypes = [vp, i32, C.POINTER(LevelSizes)]
         L.amb_export.argtypes = [vp, i32, i32, i32, vp, sz]
         L.amb_stats.argtypes = [vp, C.POINTER(KernelStats)]
@@ -216,6 +218,10 @@ class Context:
 
     def schur_apply(self, level, width, x, y):
         self._check(lib().amb_schur_apply(self.h, level, width, _ptr(x), _ptr(y)))
+
+    def schur_apply_noalloc(self, level, width, x, y):
+        """amb_schur_apply_noalloc: the same product without device allocation."""
+        self._check(lib().amb_schur_apply_noalloc(self.h, level, width, _ptr(x), _ptr(y)))
 
     def level_info(self, level=1) -> LevelSizes:
         li = LevelSizes()

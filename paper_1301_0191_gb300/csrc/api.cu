@@ -7,45 +7,13 @@
 #include <string>
 #include <vector>
 
-#include "engine.h"
+#include "ctx.h"
 #include "fem.h"
 #include "kernels.h"
 
 using namespace amb;
 
-struct amb_ctx {
-  std::string err;
-  amb_options opt;
-  cudaStream_t st = nullptr;
-  Mesh mesh;
-  EngineConfig cfg;
-  DescRing ring;
-  Timers tm;
-  std::vector<PairReportH> reports;
-  std::vector<double> omega;
-  std::vector<int> nadapt;
-  DevBuf status;
-  std::unique_ptr<EngineBase> eng;
-  DevBuf f, u, r, z, p, q, rold, tmp, partial, dscal, ab, lam, grad, body;
-  bool have_solution = false;
-  int last_its = 0;
-  double last_cond = 0, last_rel = 0;
-  int64_t launches_total = 0;
-  double setup_ms = 0;
-};
-
 namespace {
-
-bool is_device(const void* ptr) {
-  if (!ptr) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 void copy_in(DevBuf& dst, const void* src, size_t bytes, cudaStream_t st) {
   if (dst.bytes < bytes) dst.alloc(bytes);
@@ -55,25 +23,6 @@ void copy_in(DevBuf& dst, const void* src, size_t bytes, cudaStream_t st) {
 void copy_out(void* dst, const void* src, size_t bytes, cudaStream_t st) {
   AMB_CUDA(cudaMemcpyAsync(dst, src, bytes, is_device(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
   AMB_CUDA(cudaStreamSynchronize(st));
-}
-
-template <typename F>
-int guarded(amb_ctx* c, F&& fn) {
-  if (!c) return AMB_EINVAL;
-  const int64_t l0 = g_launches;
-  try {
-    c->err.clear();
-    fn();
-    c->launches_total += g_launches - l0;
-    return AMB_OK;
-  } catch (const Error& e) {
-    c->err = e.what();
-    c->launches_total += g_launches - l0;
-    return e.status;
-  } catch (const std::exception& e) {
-    c->err = e.what();
-    return AMB_EINVAL;
-  }
 }
 
 double dotd(amb_ctx* c, const double* a, const double* b, int64_t n) {
@@ -209,6 +158,7 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
               "poisson_ratio out of range");
     c->opt = *opt;
     c->st = static_cast<cudaStream_t>(opt->cuda_stream);
+    AMB_CUDA(cudaGetDevice(&c->device));
     Mesh& m = c->mesh;
     m.nx = mesh->nx;
     m.ny = mesh->ny;

@@ -154,6 +154,20 @@ template <typename T>
 void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& d, int flags,
                   T alpha, T beta, const T* A, const T* X, T* Y);
 
+// Launches on descriptor arrays already resident in device memory
+// (d_desc[ndesc], d_prefix[ndesc+1] = per-descriptor CTA prefix sums, total
+// = d_prefix[ndesc]); the *_ctas helpers give the CTA count of one
+// descriptor so callers can build the prefix sums themselves.
+template <typename T>
+int gemm_ctas(const GemmDesc& d);
+int gemv_ctas(const GemvDesc& d, bool trans);
+template <typename T>
+void gemm_launch_prepared(cudaStream_t st, const GemmDesc* d_desc, const int* d_prefix, int ndesc, int total,
+                          int flags, T alpha, T beta, const T* A, const T* B, T* C);
+template <typename T>
+void gemv_launch_prepared(cudaStream_t st, const GemvDesc* d_desc, const int* d_prefix, int ndesc, int total,
+                          int flags, T alpha, T beta, const T* A, const T* X, T* Y);
+
 // Partial blocked Cholesky of a batch of column-major matrices (dense.cu):
 // factor columns [c0, c1) of every matrix (lower), trailing updates applied
 // to the whole remaining lower triangle.  Diagonal-block inverses are

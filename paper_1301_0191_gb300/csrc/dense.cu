@@ -215,6 +215,39 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   AMB_LAUNCHED();
 }
 
+template <typename T>
+int gemm_ctas(const GemmDesc& x) {
+  using TL = GemmTile<T>;
+  if (x.m <= 0 || x.n <= 0) return 0;
+  return ((x.m + TL::BM - 1) / TL::BM) * ((x.n + TL::BN - 1) / TL::BN);
+}
+template int gemm_ctas<float>(const GemmDesc&);
+template int gemm_ctas<double>(const GemmDesc&);
+
+template <typename T>
+void gemm_launch_prepared(cudaStream_t st, const GemmDesc* d_desc, const int* d_prefix, int ndesc, int total,
+                          int flags, T alpha, T beta, const T* A, const T* B, T* C) {
+  using TL = GemmTile<T>;
+  if (ndesc <= 0 || total <= 0) return;
+  GemmArgs<T, T> g;
+  g.desc = d_desc;
+  g.prefix = d_prefix;
+  g.ndesc = ndesc;
+  g.flags = flags;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.A = A;
+  g.B = B;
+  g.C = C;
+  constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
+  k_gemm<T, T, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
+  AMB_LAUNCHED();
+}
+template void gemm_launch_prepared<float>(cudaStream_t, const GemmDesc*, const int*, int, int, int, float, float,
+                                          const float*, const float*, float*);
+template void gemm_launch_prepared<double>(cudaStream_t, const GemmDesc*, const int*, int, int, int, double, double,
+                                           const double*, const double*, double*);
+
 template void gemm_batched<float, float>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, float, float,
                                          const float*, const float*, float*);
 template void gemm_batched<double, double>(cudaStream_t, DescRing&, const std::vector<GemmDesc>&, int, double,
@@ -354,6 +387,26 @@ void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& 
   else k_gemv_n<T><<<(unsigned)total, kGemvRows, 0, st>>>(g);
   AMB_LAUNCHED();
 }
+
+int gemv_ctas(const GemvDesc& x, bool trans) {
+  const int outs = trans ? x.n : x.m;
+  if (outs <= 0) return 0;
+  return trans ? (outs + kGemvCols - 1) / kGemvCols : (outs + kGemvRows - 1) / kGemvRows;
+}
+
+template <typename T>
+void gemv_launch_prepared(cudaStream_t st, const GemvDesc* d_desc, const int* d_prefix, int ndesc, int total,
+                          int flags, T alpha, T beta, const T* A, const T* X, T* Y) {
+  if (ndesc <= 0 || total <= 0) return;
+  GemvArgs<T> g{d_desc, d_prefix, ndesc, flags, alpha, beta, A, X, Y};
+  if (flags & G_TRANS_A) k_gemv_t<T><<<(unsigned)total, 32 * kGemvCols, 0, st>>>(g);
+  else k_gemv_n<T><<<(unsigned)total, kGemvRows, 0, st>>>(g);
+  AMB_LAUNCHED();
+}
+template void gemv_launch_prepared<float>(cudaStream_t, const GemvDesc*, const int*, int, int, int, float, float,
+                                          const float*, const float*, float*);
+template void gemv_launch_prepared<double>(cudaStream_t, const GemvDesc*, const int*, int, int, int, double, double,
+                                           const double*, const double*, double*);
 
 template void gemv_batched<float>(cudaStream_t, DescRing&, const std::vector<GemvDesc>&, int, float, float,
                                   const float*, const float*, float*);

@@ -561,6 +561,50 @@ void Engine<T>::schur_apply(int level, int width, const void* x, void* y) {
   tm.fam_bytes[AMB_FAM_SCHUR] += by;
 }
 
+template <typename T>
+void Engine<T>::schur_apply_staged(int level, int width, const void* x, void* y, void* scratch, size_t bytes) {
+  AMB_CHECK(level >= 1 && level <= (int)lv.size(), AMB_EINVAL, "level out of range");
+  AMB_CHECK(width >= 1, AMB_EINVAL, "width must be >= 1");
+  const LevelData<T>& L = *lv[level - 1];
+  AMB_CHECK(L.ns <= kStagedMaxDesc, AMB_EINVAL,
+            "more than " + std::to_string(kStagedMaxDesc) + " substructures on the level");
+  // descriptors are built on the host stack: no heap or device allocation
+  GemmDesc gd[kStagedMaxDesc];
+  GemvDesc vd[kStagedMaxDesc];
+  int prefix[kStagedMaxDesc + 1];
+  int nd = 0, total = 0;
+  int64_t off = 0;
+  for (int s = 0; s < L.ns; ++s) {
+    const int ng = L.ng[s];
+    if (ng == 0) continue;
+    prefix[nd] = total;
+    if (width == 1) {
+      vd[nd] = GemvDesc{ng, ng, ng, 0, L.pS.off[s], off, off};
+      total += gemv_ctas(vd[nd], false);
+    } else {
+      gd[nd] = GemmDesc{ng, width, ng, ng, ng, ng, L.pS.off[s], off, off};
+      total += gemm_ctas<T>(gd[nd]);
+    }
+    off += (int64_t)ng * width;
+    ++nd;
+  }
+  prefix[nd] = total;
+  if (nd == 0) return;
+  const size_t dbytes = (size_t)nd * (width == 1 ? sizeof(GemvDesc) : sizeof(GemmDesc));
+  const size_t poff = (dbytes + 255) & ~size_t(255);
+  AMB_CHECK(poff + (size_t)(nd + 1) * sizeof(int) <= bytes, AMB_EINVAL, "launch descriptors exceed the scratch size");
+  char* sc = static_cast<char*>(scratch);
+  AMB_CUDA(cudaMemcpyAsync(sc, width == 1 ? (const void*)vd : (const void*)gd, dbytes, cudaMemcpyHostToDevice, st));
+  AMB_CUDA(cudaMemcpyAsync(sc + poff, prefix, (size_t)(nd + 1) * sizeof(int), cudaMemcpyHostToDevice, st));
+  const int* dpre = reinterpret_cast<const int*>(sc + poff);
+  if (width == 1)
+    gemv_launch_prepared<T>(st, reinterpret_cast<const GemvDesc*>(sc), dpre, nd, total, 0, T(1), T(0),
+                            dptr<T>(L.S), static_cast<const T*>(x), static_cast<T*>(y));
+  else
+    gemm_launch_prepared<T>(st, reinterpret_cast<const GemmDesc*>(sc), dpre, nd, total, 0, T(1), T(0),
+                            dptr<T>(L.S), static_cast<const T*>(x), static_cast<T*>(y));
+}
+
 // ------------------------------------------------------------------ exports
 
 template <typename T>

@@ -70,11 +70,17 @@ class EngineBase {
   virtual void setup() = 0;
   virtual void precond(const double* r, double* z) = 0;   // device full-grid vectors
   virtual void schur_apply(int level, int width, const void* x, void* y) = 0;
+  // Same product, with the launch descriptors staged in caller-provided
+  // device memory `scratch` (bytes) instead of the context's staging ring.
+  virtual void schur_apply_staged(int level, int width, const void* x, void* y, void* scratch, size_t bytes) = 0;
   virtual const LevelTopo& topo(int level) const = 0;
   virtual int n_levels() const = 0;
   virtual void export_sub(int what, int level, int idx, std::vector<char>& out) = 0;
   virtual double level_factor_flops(int level) const = 0;
 };
+
+// Largest number of substructures per level the staged Schur apply accepts.
+constexpr int kStagedMaxDesc = 1024;
 
 struct EngineConfig {
   amb_options opt;

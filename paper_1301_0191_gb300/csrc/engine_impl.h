@@ -20,6 +20,7 @@ class Engine : public EngineBase {
   void setup() override;
   void precond(const double* r, double* z) override { apply_level(0, r, z); }
   void schur_apply(int level, int width, const void* x, void* y) override;
+  void schur_apply_staged(int level, int width, const void* x, void* y, void* scratch, size_t bytes) override;
   const LevelTopo& topo(int level) const override { return lv[level - 1]->topo; }
   int n_levels() const override { return (int)lv.size(); }
   void export_sub(int what, int level, int idx, std::vector<char>& out) override;
