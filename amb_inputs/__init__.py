@@ -266,5 +266,20 @@ def toy(sub_elems: int, dpn: int, seed: int, split=(2, 1, 1), sigma: float = 1.0
                    levels=levels, tau=tau)
 
 
+def sub_block(prob: Problem, nb: Sequence[int]) -> Problem:
+    """The corner block of nb[0] x nb[1] x nb[2] level-1 boxes of a workload
+    (the block at x = 0, so it keeps the Dirichlet face): same substructure
+    shapes and coefficients, two levels."""
+    cuts = [np.asarray(prob.cuts[0][a])[: nb[a] + 1] for a in range(3)]
+    nx, ny, nz = (int(c[-1]) for c in cuts)
+    coeff = prob.coeff.reshape(prob.nz, prob.ny, prob.nx)[:nz, :ny, :nx].ravel().copy()
+    body = prob.body.reshape(prob.nz, prob.ny, prob.nx, -1)[:nz, :ny, :nx].reshape(nx * ny * nz, -1).copy()
+    p = Problem(name=f"{prob.name}_block{nb[0]}x{nb[1]}x{nb[2]}", nx=nx, ny=ny, nz=nz,
+                dofs_per_node=prob.dofs_per_node, coeff=coeff, poisson_ratio=prob.poisson_ratio, body=body,
+                dirichlet_node_mask=_dirichlet_x0(nx, ny, nz), cuts=[[c - c[0] for c in cuts]],
+                elem_to_sub=tensor_partition(nx, ny, nz, cuts), sub_to_parent=[], levels=2, tau=prob.tau)
+    return p
+
+
 def random_vector(n: int, seed: int) -> np.ndarray:
     return np.random.default_rng(np.random.PCG64(seed)).standard_normal(n)

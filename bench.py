@@ -95,15 +95,8 @@ def oracle_sample(prob, reps=1):
     extrapolated to 64 substructures and the oracle's own iteration count on
     the full workload (37, tests/golden)."""
     from oracle import fe, solver
-    sub = ai.Problem(name="sample", nx=24, ny=24, nz=12, dofs_per_node=3,
-                     coeff=prob.coeff.reshape(48, 48, 48)[:12, :24, :24].ravel().copy(),
-                     poisson_ratio=prob.poisson_ratio, body=prob.body[: 24 * 24 * 12].copy(),
-                     dirichlet_node_mask=None, cuts=[[np.array([0, 12, 24]), np.array([0, 12, 24]),
-                                                      np.array([0, 12])]],
-                     elem_to_sub=None, sub_to_parent=[], levels=2, tau=prob.tau)
-    sub.dirichlet_node_mask = ai._dirichlet_x0(24, 24, 12)
-    sub.elem_to_sub = ai.tensor_partition(24, 24, 12, sub.cuts[0])
-    its_full = 37   # the element size only scales K, not the work
+    sub = ai.sub_block(prob, (2, 2, 1))
+    its_full = 37   # the oracle's PCG iterations on the full workload (tests/golden)
     t0 = time.perf_counter()
     h = solver.Hierarchy(sub)
     t_setup = time.perf_counter() - t0
@@ -135,11 +128,20 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2block"],
+                    help="c2: the 48^3 workload; c2block: its 2x1x1 corner block (two of its substructures, "
+                         "same shapes, ~0.5 GB on the device), for profiler captures")
+    ap.add_argument("--profile", action="store_true",
+                    help="warm-up + timed steps only (no e2e, family timing, Schur sweep or baselines)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     prob = ai.config(2)
+    workload = WORKLOAD
+    if args.workload == "c2block":
+        prob = ai.sub_block(prob, (2, 1, 1))
+        workload = prob.name
 
     if args.impl == "reference":
         if rank != 0:
@@ -216,6 +218,14 @@ def main():
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": ms * 1e-3, "unit": "s", "profile_run": True,
+                              "config": {"workload": workload}, "pcg_iterations": infos[-1].iterations,
+                              "gpu_launches": int(launches / args.steps)}))
+        if world > 1:
+            dist.destroy_process_group()
+        return
 
     # end to end: host coefficients / rhs / solution, copies inside the timed region
     coeff_h = np.ascontiguousarray(prob.coeff)
@@ -297,7 +307,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == B.FP32 else "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "levels": 2, "tau": 10.0, "dofs": int(li.n_dofs),
+                "config": {"workload": workload, "levels": 2, "tau": 10.0, "dofs": int(li.n_dofs),
                            "substructures": li.n_subs, "pairs": li.n_pairs, "l2": "working set >> L2 (no flush)",
                            "replicas": "one independent problem per GPU"},
                 "pcg_iterations": last.iterations, "rel_residual": last.rel_residual,
