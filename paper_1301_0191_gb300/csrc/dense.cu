@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "common.h"
 
@@ -173,6 +174,116 @@ k_gemm(GemmArgs<T, TA> g) {
   }
 }
 
+// ------------------------------------------------------------------ GEMM, FP32 operands, extended accumulation
+// C (FP64) = alpha op(A) op(B) + beta C with A stored in FP32 and B in FP64.
+// FP64 arithmetic runs at 1/64 of the FP32 rate on this GPU, so the sum is
+// carried in FP32 pairs instead: every product a*b_hi is split exactly into
+// p + e with an FMA, added to (hi, lo) by Knuth's TwoSum, and a*b_lo (b =
+// b_hi + b_lo, both FP32) goes into lo.  The result hi + lo has about 44
+// significant bits, enough for the FP64-consistent Rayleigh-Ritz of the
+// pair eigenproblems; plain FP32 accumulation is not (see lobpcg.cu).
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_gemm_df(GemmArgs<double, float> g) {
+  constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
+  constexpr int LA = BM * BK / NT, LB = BK * BN / NT;
+  static_assert(LA * NT == BM * BK && LB * NT == BK * BN, "tile/thread mismatch");
+  __shared__ float As[BK][BM + 4];
+  __shared__ float2 Bs[BK][BN + 2];
+  const int bid = blockIdx.x;
+  int lo = 0, hi = g.ndesc - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (g.prefix[mid] <= bid) lo = mid; else hi = mid - 1;
+  }
+  const GemmDesc d = g.desc[lo];
+  const int t = bid - g.prefix[lo];
+  const int tn = (d.n + BN - 1) / BN;
+  const int i0 = (t / tn) * BM, j0 = (t % tn) * BN;
+  const int fl = g.flags;
+  const bool ta = fl & G_TRANS_A, tb = fl & G_TRANS_B;
+  int kbeg = 0, kend = d.k;
+  if (fl & G_TRI_A_LOWER) kend = min(kend, i0 + BM);
+  if (fl & G_TRI_B_UPPER) kend = min(kend, j0 + BN);
+  if (fl & G_TRI_A_UPPER) kbeg = max(kbeg, (i0 / BK) * BK);
+  if (fl & G_TRI_B_LOWER) kbeg = max(kbeg, (j0 / BK) * BK);
+  const float* __restrict__ A = g.A + d.a;
+  const double* __restrict__ B = g.B + d.b;
+  const int tid = threadIdx.x, tx = tid % NTX, ty = tid / NTX;
+  float ah[TM][TN], al[TM][TN];
+#pragma unroll
+  for (int p = 0; p < TM; ++p)
+#pragma unroll
+    for (int q = 0; q < TN; ++q) ah[p][q] = al[p][q] = 0.f;
+  for (int kt = kbeg; kt < kend; kt += BK) {
+#pragma unroll
+    for (int q = 0; q < LA; ++q) {
+      int idx = tid + q * NT, r, c;
+      if (!ta) { r = idx % BM; c = idx / BM; } else { c = idx % BK; r = idx / BK; }
+      int gi = i0 + r, gk = kt + c;
+      bool ok = gi < d.m && gk < kend;
+      if ((fl & G_TRI_A_LOWER) && gk > gi) ok = false;
+      if ((fl & G_TRI_A_UPPER) && gk < gi) ok = false;
+      float v = 0.f;
+      if (ok) v = ta ? A[gk + (int64_t)gi * d.lda] : A[gi + (int64_t)gk * d.lda];
+      As[c][r] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < LB; ++q) {
+      int idx = tid + q * NT, c, j;
+      if (!tb) { c = idx % BK; j = idx / BK; } else { j = idx % BN; c = idx / BN; }
+      int gk = kt + c, gj = j0 + j;
+      bool ok = gj < d.n && gk < kend;
+      if ((fl & G_TRI_B_LOWER) && gk < gj) ok = false;
+      if ((fl & G_TRI_B_UPPER) && gk > gj) ok = false;
+      double v = 0.0;
+      if (ok) v = tb ? B[gj + (int64_t)gk * d.ldb] : B[gk + (int64_t)gj * d.ldb];
+      const float vh = (float)v;
+      Bs[c][j] = make_float2(vh, (float)(v - (double)vh));
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM];
+      float2 b[TN];
+#pragma unroll
+      for (int p = 0; p < TM; ++p) a[p] = As[kk][tx * TM + p];
+#pragma unroll
+      for (int q = 0; q < TN; ++q) b[q] = Bs[kk][ty * TN + q];
+#pragma unroll
+      for (int p = 0; p < TM; ++p)
+#pragma unroll
+        for (int q = 0; q < TN; ++q) {
+          // explicit _rn intrinsics: never contracted into FMAs, so the
+          // error-free transformations stay exact
+          const float pr = __fmul_rn(a[p], b[q].x);
+          const float e = fmaf(a[p], b[q].x, -pr);
+          const float s = __fadd_rn(ah[p][q], pr);
+          const float bb = __fsub_rn(s, ah[p][q]);
+          const float er = __fadd_rn(__fsub_rn(ah[p][q], __fsub_rn(s, bb)), __fsub_rn(pr, bb));
+          ah[p][q] = s;
+          al[p][q] = fmaf(a[p], b[q].y, __fadd_rn(al[p][q], __fadd_rn(er, e)));
+        }
+    }
+    __syncthreads();
+  }
+  double* C = g.C + d.c;
+#pragma unroll
+  for (int q = 0; q < TN; ++q) {
+    int j = j0 + ty * TN + q;
+    if (j >= d.n) continue;
+#pragma unroll
+    for (int p = 0; p < TM; ++p) {
+      int i = i0 + tx * TM + p;
+      if (i >= d.m) continue;
+      int64_t o = i + (int64_t)j * d.ldc;
+      double v = g.alpha * ((double)ah[p][q] + (double)al[p][q]);
+      if (g.beta != 0.0) v = fma(g.beta, C[o], v);
+      C[o] = v;
+    }
+  }
+}
+
 template <typename T> struct GemmTile;
 template <> struct GemmTile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
@@ -211,6 +322,13 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   g.B = B;
   g.C = C;
   constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
+  if constexpr (std::is_same<T, double>::value && std::is_same<TA, float>::value) {
+    if ((flags & G_OUT_LOWER) == 0) {   // extended-precision FP32 path (same 64x64 tiling)
+      k_gemm_df<TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
+      AMB_LAUNCHED();
+      return;
+    }
+  }
   k_gemm<T, TA, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
   AMB_LAUNCHED();
 }

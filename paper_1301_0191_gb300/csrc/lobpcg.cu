@@ -333,8 +333,11 @@ __global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const 
   }
 }
 
-// FP64 Gram matrices G = U^T V over the first w columns of the panel;
-// kind 0: V = A-block, kind 1: V = B-block.
+// Gram matrices G = U^T V over the first w columns of the panel (kind 0:
+// V = A-block, kind 1: V = B-block), upper triangle computed and mirrored.
+// The FP64 entries are split into FP32 pairs (x = x_h + x_l) and the dot
+// products carried in FP32 pairs (exact x_h*y_h by FMA, TwoSum, cross terms
+// into the low word): about 46 significant bits, at FP32 throughput.
 template <typename T>
 __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int w, const int* act) {
   const int p = blockIdx.x, kind = blockIdx.y;
@@ -343,35 +346,59 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
   const int m3 = 3 * m;
   const T* U = Qb + QP(p, Q_OQ);
   const T* Vb = U + (int64_t)(kind ? 6 * m : 3 * m) * N;
-  __shared__ double us[32][3 * AMB_MAX_EIG + 1], vs[32][3 * AMB_MAX_EIG + 1];
-  constexpr int NQ = (9 * AMB_MAX_EIG * AMB_MAX_EIG + 255) / 256;
-  double acc[NQ];
-  for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
-  const int nout = w * w;
+  __shared__ float2 us[32][3 * AMB_MAX_EIG + 1], vs[32][3 * AMB_MAX_EIG + 1];
+  constexpr int NQ = (3 * AMB_MAX_EIG * (3 * AMB_MAX_EIG + 1) / 2 + 255) / 256;
+  float hi[NQ], lo[NQ];
+  int oa[NQ], ob[NQ];
+  const int nout = w * (w + 1) / 2;
+  for (int q = 0; q < NQ; ++q) {
+    hi[q] = lo[q] = 0.f;
+    const int o = threadIdx.x + q * blockDim.x;
+    int b = (int)((sqrtf(8.f * o + 1.f) - 1.f) * 0.5f);
+    while (b * (b + 1) / 2 > o) --b;
+    while ((b + 1) * (b + 2) / 2 <= o) ++b;
+    oa[q] = o - b * (b + 1) / 2;
+    ob[q] = b;
+  }
   for (int64_t r0 = 0; r0 < N; r0 += 32) {
     const int rn = (N - r0) < 32 ? (int)(N - r0) : 32;
     for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
-      int r = idx % 32, c = idx / 32;
-      us[r][c] = r < rn ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
-      vs[r][c] = r < rn ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
+      const int r = idx % 32, c = idx / 32;
+      const double u = r < rn ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
+      const double v = r < rn ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
+      const float uh = (float)u, vh = (float)v;
+      us[r][c] = make_float2(uh, (float)(u - (double)uh));
+      vs[r][c] = make_float2(vh, (float)(v - (double)vh));
     }
     __syncthreads();
+#pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      int o = threadIdx.x + q * blockDim.x;
+      const int o = threadIdx.x + q * blockDim.x;
       if (o >= nout) break;
-      int a = o % w, b = o / w;
-      double s = acc[q];
-      for (int r = 0; r < rn; ++r) s = fma(us[r][a], vs[r][b], s);
-      acc[q] = s;
+      const int a = oa[q], b = ob[q];
+      float h = hi[q], l = lo[q];
+      for (int r = 0; r < rn; ++r) {
+        const float2 x = us[r][a], y = vs[r][b];
+        const float pr = __fmul_rn(x.x, y.x);
+        const float e = fmaf(x.x, y.x, -pr);
+        const float s = __fadd_rn(h, pr);
+        const float bb = __fsub_rn(s, h);
+        const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(pr, bb));
+        h = s;
+        l = fmaf(x.x, y.y, fmaf(x.y, y.x, __fadd_rn(l, __fadd_rn(er, e))));
+      }
+      hi[q] = h;
+      lo[q] = l;
     }
     __syncthreads();
   }
   double* g = G + QP(p, Q_OGR) + (int64_t)kind * m3 * m3;
   for (int q = 0; q < NQ; ++q) {
-    int o = threadIdx.x + q * blockDim.x;
+    const int o = threadIdx.x + q * blockDim.x;
     if (o >= nout) break;
-    int a = o % w, b = o / w;
-    g[a + b * m3] = acc[q];
+    const double v = (double)hi[q] + (double)lo[q];
+    g[oa[q] + ob[q] * m3] = v;
+    g[ob[q] + oa[q] * m3] = v;
   }
 }
 
@@ -619,8 +646,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const int m = std::min(AMB_MAX_EIG, maxad + 1 + 4);
   const int m3 = 3 * m;
   // SVQB: directions whose scaled B-Gram eigenvalue is below drop * max are
-  // numerically dependent at the storage precision and are discarded
-  const double svqb_drop = sizeof(T) == 4 ? 1e-5 : 1e-10;
+  // numerically dependent and are discarded.  The Gram matrices come from
+  // FP64 vectors and extended-precision operator products in both forms.
+  const double svqb_drop = 1e-10;
   // ------------------------------------------------ pair tables
   std::vector<int64_t> qp((size_t)np * Q_NPAIRF, 0);
   std::vector<int32_t> hps, hpt, hgoff(1, 0), hgent, hface, hcms, hcmt;
@@ -951,12 +979,12 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   applyB(0, 6);
   rayleigh_ritz(m);
   std::vector<double> hl((size_t)np * m), hr((size_t)np * m), hb((size_t)np * m);
-  // Residuals of FP32 block vectors cannot fall far below sqrt(eps_32); the
-  // residual target is clamped to what the storage precision can reach.
-  const double tol = sizeof(T) == 4 ? std::max(cfg.opt.lobpcg_tol, 1e-4) : cfg.opt.lobpcg_tol;
+  const double tol = cfg.opt.lobpcg_tol;
   const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
   const double tau = cfg.tau;
-  std::vector<double> resid(np, 0.0);
+  std::vector<double> resid(np, 0.0), best(np, 1e300);
+  std::vector<int> since(np, 0);
+  constexpr int kStall = 20;
   auto check = [&]() {
     k_lob_resid<V><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
@@ -984,7 +1012,15 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       }
       resid[p] = worst;
       conv[p] = ok ? 1 : 0;
-      active[p] = ok ? 0 : 1;
+      // stagnation: a pair whose worst used residual has not halved within
+      // kStall iterations stops iterating (reported as not converged)
+      if (worst < 0.5 * best[p]) {
+        best[p] = worst;
+        since[p] = 0;
+      } else {
+        ++since[p];
+      }
+      active[p] = (ok || since[p] >= kStall) ? 0 : 1;
       nact += active[p];
     }
     return nact;
