@@ -402,6 +402,111 @@ __device__ inline int gemv_find(const GemvArgs<T>& g, int bid) {
   return lo;
 }
 
+// Compensated accumulation for FP32 matrix-vector products: (hi, lo) holds
+// the running sum, products are split exactly by FMA and added by TwoSum.
+// The GEMVs stream their matrix from HBM, so the extra FP32 instructions
+// are hidden behind memory traffic.
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float pr = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -pr);
+    const float s = __fadd_rn(hi, pr);
+    const float bb = __fsub_rn(s, hi);
+    const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(pr, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(er, e));
+  }
+  __device__ __forceinline__ void merge(const DF& o) {
+    const float s = __fadd_rn(hi, o.hi);
+    const float bb = __fsub_rn(s, hi);
+    const float er = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(o.hi, bb));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(er, o.lo));
+  }
+  __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
+};
+
+__global__ void __launch_bounds__(kGemvRows) k_gemv_n_df(GemvArgs<float> g) {
+  __shared__ float xs[1024];
+  int lo_d = 0, hi_d = g.ndesc - 1;
+  while (lo_d < hi_d) {
+    int mid = (lo_d + hi_d + 1) >> 1;
+    if (g.prefix[mid] <= (int)blockIdx.x) lo_d = mid; else hi_d = mid - 1;
+  }
+  const GemvDesc d = g.desc[lo_d];
+  const int rb = blockIdx.x - g.prefix[lo_d];
+  const int i = rb * kGemvRows + threadIdx.x;
+  const float* __restrict__ A = g.A + d.a;
+  const float* __restrict__ x = g.X + d.x;
+  int lend = d.n;
+  if (g.flags & G_TRI_A_LOWER) lend = min(d.n, rb * kGemvRows + kGemvRows);
+  int lbeg = 0;
+  if (g.flags & G_TRI_A_UPPER) lbeg = rb * kGemvRows;
+  DF s0, s1;
+  for (int c0 = lbeg; c0 < lend; c0 += 1024) {
+    int cn = min(1024, lend - c0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cn; q += kGemvRows) xs[q] = x[c0 + q];
+    __syncthreads();
+    if (i < d.m) {
+      int cl = 0, ch = cn;
+      if (g.flags & G_TRI_A_LOWER) ch = min(cn, i - c0 + 1);
+      if (g.flags & G_TRI_A_UPPER) cl = max(0, i - c0);
+      const float* col = A + i + (int64_t)(c0 + cl) * d.lda;
+      int q = cl;
+      for (; q + 1 < ch; q += 2) {
+        s0.add(col[0], xs[q]);
+        s1.add(col[d.lda], xs[q + 1]);
+        col += 2 * (int64_t)d.lda;
+      }
+      for (; q < ch; ++q) {
+        s0.add(col[0], xs[q]);
+        col += d.lda;
+      }
+    }
+  }
+  if (i < d.m) {
+    s0.merge(s1);
+    float v = g.alpha * s0.value();
+    float* y = g.Y + d.y;
+    if (g.beta != 0.f) v = fmaf(g.beta, y[i], v);
+    y[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t_df(GemvArgs<float> g) {
+  int lo_d = 0, hi_d = g.ndesc - 1;
+  while (lo_d < hi_d) {
+    int mid = (lo_d + hi_d + 1) >> 1;
+    if (g.prefix[mid] <= (int)blockIdx.x) lo_d = mid; else hi_d = mid - 1;
+  }
+  const GemvDesc d = g.desc[lo_d];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int j = (blockIdx.x - g.prefix[lo_d]) * kGemvCols + warp;
+  if (j >= d.n) return;
+  const float* __restrict__ col = g.A + d.a + (int64_t)j * d.lda;
+  const float* __restrict__ x = g.X + d.x;
+  int ib = 0, ie = d.m;
+  if (g.flags & G_TRI_A_UPPER) ib = min(j, d.m);
+  if (g.flags & G_TRI_A_LOWER) ie = min(d.m, j + 1);
+  DF s;
+  for (int i = ib + lane; i < ie; i += 32) s.add(col[i], x[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF t;
+    t.hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
+    t.lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
+    s.merge(t);
+  }
+  if (lane == 0) {
+    float v = g.alpha * s.value();
+    float* y = g.Y + d.y;
+    if (g.beta != 0.f) v = fmaf(g.beta, y[j], v);
+    y[j] = v;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kGemvRows) k_gemv_n(GemvArgs<T> g) {
   __shared__ T xs[1024];
@@ -478,6 +583,18 @@ __global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t(GemvArgs<T> g) {
   }
 }
 
+// FP32 products use the compensated kernels, FP64 the plain ones.
+template <typename T>
+static void launch_gemv(cudaStream_t st, const GemvArgs<T>& g, unsigned total, bool trans) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (trans) k_gemv_t_df<<<total, 32 * kGemvCols, 0, st>>>(g);
+    else k_gemv_n_df<<<total, kGemvRows, 0, st>>>(g);
+  } else {
+    if (trans) k_gemv_t<T><<<total, 32 * kGemvCols, 0, st>>>(g);
+    else k_gemv_n<T><<<total, kGemvRows, 0, st>>>(g);
+  }
+}
+
 template <typename T>
 void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& d, int flags,
                   T alpha, T beta, const T* A, const T* X, T* Y) {
@@ -501,8 +618,8 @@ void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& 
   GemvArgs<T> g{reinterpret_cast<const GemvDesc*>(dev),
                 reinterpret_cast<const int*>(dev + dd.size() * sizeof(GemvDesc)),
                 (int)dd.size(), flags, alpha, beta, A, X, Y};
-  if (trans) k_gemv_t<T><<<(unsigned)total, 32 * kGemvCols, 0, st>>>(g);
-  else k_gemv_n<T><<<(unsigned)total, kGemvRows, 0, st>>>(g);
+  launch_gemv<T>(st, g, (unsigned)total, trans);
+
   AMB_LAUNCHED();
 }
 
@@ -517,8 +634,8 @@ void gemv_launch_prepared(cudaStream_t st, const GemvDesc* d_desc, const int* d_
                           int flags, T alpha, T beta, const T* A, const T* X, T* Y) {
   if (ndesc <= 0 || total <= 0) return;
   GemvArgs<T> g{d_desc, d_prefix, ndesc, flags, alpha, beta, A, X, Y};
-  if (flags & G_TRANS_A) k_gemv_t<T><<<(unsigned)total, 32 * kGemvCols, 0, st>>>(g);
-  else k_gemv_n<T><<<(unsigned)total, kGemvRows, 0, st>>>(g);
+  launch_gemv<T>(st, g, (unsigned)total, (flags & G_TRANS_A) != 0);
+
   AMB_LAUNCHED();
 }
 template void gemv_launch_prepared<float>(cudaStream_t, const GemvDesc*, const int*, int, int, int, float, float,
