@@ -138,10 +138,15 @@ k_gemm(GemmArgs<T, TA> g) {
           V v = *reinterpret_cast<const V*>(&As[buf][kk][tx * TM + p]);
           memcpy(&a[p], &v, sizeof(V));
         }
+        if constexpr (TN % W == 0) {
 #pragma unroll
-        for (int q = 0; q < TN; q += W) {
-          V v = *reinterpret_cast<const V*>(&Bs[buf][kk][ty * TN + q]);
-          memcpy(&b[q], &v, sizeof(V));
+          for (int q = 0; q < TN; q += W) {
+            V v = *reinterpret_cast<const V*>(&Bs[buf][kk][ty * TN + q]);
+            memcpy(&b[q], &v, sizeof(V));
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < TN; ++q) b[q] = Bs[buf][kk][ty * TN + q];
         }
 #pragma unroll
         for (int p = 0; p < TM; ++p)
@@ -288,10 +293,16 @@ template <typename T> struct GemmTile;
 template <> struct GemmTile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
 
-template <typename T, typename TA>
-void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
-                  T alpha, T beta, const TA* A, const T* B, T* C) {
-  using TL = GemmTile<T>;
+// Tile shapes: a wide one, and a skinny one for products whose right-hand
+// block has at most 16 columns (the LOBPCG blocks and the Neumann solves of
+// the pair preconditioner), which would otherwise waste most of a wide tile.
+template <typename T> struct GemmSkinny;
+template <> struct GemmSkinny<double> { static constexpr int BM = 64, BN = 16, BK = 16, TM = 4, TN = 2; };
+template <> struct GemmSkinny<float> { static constexpr int BM = 128, BN = 16, BK = 16, TM = 8, TN = 2; };
+
+template <typename T, typename TA, typename TL>
+static void gemm_run(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags, T alpha, T beta,
+                     const TA* A, const T* B, T* C) {
   std::vector<GemmDesc> dd;
   std::vector<int> prefix;
   dd.reserve(d.size());
@@ -323,7 +334,7 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   g.C = C;
   constexpr int NT = (TL::BM / TL::TM) * (TL::BN / TL::TN);
   if constexpr (std::is_same<T, double>::value && std::is_same<TA, float>::value) {
-    if ((flags & G_OUT_LOWER) == 0) {   // extended-precision FP32 path (same 64x64 tiling)
+    if ((flags & G_OUT_LOWER) == 0) {   // extended-precision FP32 path
       k_gemm_df<TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
       AMB_LAUNCHED();
       return;
@@ -331,6 +342,17 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   }
   k_gemm<T, TA, TL::BM, TL::BN, TL::BK, TL::TM, TL::TN><<<(unsigned)total, NT, 0, st>>>(g);
   AMB_LAUNCHED();
+}
+
+template <typename T, typename TA>
+void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
+                  T alpha, T beta, const TA* A, const T* B, T* C) {
+  int nmax = 0;
+  for (const auto& x : d) nmax = std::max(nmax, x.n);
+  if (nmax <= 16 && !(flags & G_OUT_LOWER))
+    gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C);
+  else
+    gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C);
 }
 
 template <typename T>
@@ -738,50 +760,76 @@ static T* diag_scratch(size_t nblocks) {
 template <typename T>
 void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDesc>& d, T* base,
                       T* zbase, int* status, double* flops) {
+  // Two-level blocking: inner panels of kNB columns (diagonal factor +
+  // inverse, panel solve) inside outer blocks of kOuter columns.  Inside an
+  // outer block the next panel's columns are brought up to date from the
+  // previous panels of the block (left-looking strip update); the trailing
+  // matrix is updated once per outer block with K = kOuter, which cuts the
+  // passes over the trailing matrix (and its memory traffic) by kOuter/kNB.
+  constexpr int kOuter = 4 * kNB;
   if (d.empty()) return;
-  int maxsteps = 0;
-  for (const auto& x : d) maxsteps = std::max(maxsteps, (x.c1 - x.c0 + kNB - 1) / kNB);
+  int maxouter = 0;
+  for (const auto& x : d) maxouter = std::max(maxouter, (x.c1 - x.c0 + kOuter - 1) / kOuter);
   T* scratch = diag_scratch<T>(d.size());
-  for (int step = 0; step < maxsteps; ++step) {
-    std::vector<DiagDesc> dg;
-    std::vector<GemmDesc> panel, trail;
-    for (size_t q = 0; q < d.size(); ++q) {
-      const CholDesc& x = d[q];
-      const int j0 = x.c0 + step * kNB;
-      if (j0 >= x.c1) continue;
-      const int jb = std::min(kNB, x.c1 - j0);
-      DiagDesc g;
-      g.blk = x.off + j0 + (int64_t)j0 * x.ld;
-      g.zblk = zbase ? x.zoff + (int64_t)step * kNB * (x.zld + 1) : -1;
-      g.scratch = (int64_t)q * kNB * kNB;
-      g.ld = x.ld;
-      g.zld = x.zld;
-      g.jb = jb;
-      g.id = x.id;
-      g.col = j0;
-      dg.push_back(g);
-      const int r0 = j0 + jb, rem = x.n - r0;
-      if (rem > 0) {
-        // panel: P := P * Dinv^T  (rows r0.., columns j0..j0+jb), in place
-        GemmDesc p{rem, jb, jb, x.ld, kNB, x.ld, x.off + r0 + (int64_t)j0 * x.ld, (int64_t)q * kNB * kNB,
-                   x.off + r0 + (int64_t)j0 * x.ld};
-        panel.push_back(p);
-        // trailing lower update: C -= P P^T
-        GemmDesc u{rem, rem, jb, x.ld, x.ld, x.ld, x.off + r0 + (int64_t)j0 * x.ld,
-                   x.off + r0 + (int64_t)j0 * x.ld, x.off + r0 + (int64_t)r0 * x.ld};
-        trail.push_back(u);
-        if (flops) *flops += (double)rem * jb * jb + (double)rem * (rem + 1) * jb;
+  for (int ob = 0; ob < maxouter; ++ob) {
+    for (int q = 0; q < kOuter / kNB; ++q) {
+      std::vector<DiagDesc> dg;
+      std::vector<GemmDesc> strip, panel;
+      for (size_t i = 0; i < d.size(); ++i) {
+        const CholDesc& x = d[i];
+        const int J0 = x.c0 + ob * kOuter;
+        if (J0 >= x.c1) continue;
+        const int J1 = std::min(J0 + kOuter, x.c1);
+        const int j0 = J0 + q * kNB;
+        if (j0 >= J1) continue;
+        const int jb = std::min(kNB, J1 - j0);
+        const int rem0 = x.n - j0;   // rows from the diagonal block down
+        if (j0 > J0) {
+          // A[j0:, j0:j0+jb] -= A[j0:, J0:j0] A[j0:j0+jb, J0:j0]^T
+          strip.push_back(GemmDesc{rem0, jb, j0 - J0, x.ld, x.ld, x.ld, x.off + j0 + (int64_t)J0 * x.ld,
+                                   x.off + j0 + (int64_t)J0 * x.ld, x.off + j0 + (int64_t)j0 * x.ld});
+          if (flops) *flops += 2.0 * rem0 * jb * (j0 - J0);
+        }
+        DiagDesc g;
+        g.blk = x.off + j0 + (int64_t)j0 * x.ld;
+        g.zblk = zbase ? x.zoff + (int64_t)(j0 - x.c0) * (x.zld + 1) : -1;
+        g.scratch = (int64_t)i * kNB * kNB;
+        g.ld = x.ld;
+        g.zld = x.zld;
+        g.jb = jb;
+        g.id = x.id;
+        g.col = j0;
+        dg.push_back(g);
+        const int r0 = j0 + jb, rem = x.n - r0;
+        if (rem > 0) {
+          panel.push_back(GemmDesc{rem, jb, jb, x.ld, kNB, x.ld, x.off + r0 + (int64_t)j0 * x.ld, (int64_t)i * kNB * kNB,
+                                   x.off + r0 + (int64_t)j0 * x.ld});
+          if (flops) *flops += (double)rem * jb * jb;
+        }
+        if (flops) *flops += (double)jb * jb * jb / 3.0;
       }
-      if (flops) *flops += (double)jb * jb * jb / 3.0;
+      if (dg.empty()) continue;
+      if (!strip.empty())
+        gemm_batched<T>(st, ring, strip, G_TRANS_B, T(-1), T(1), base, base, base);
+      const DiagDesc* ddev = static_cast<const DiagDesc*>(ring.push(dg.data(), dg.size() * sizeof(DiagDesc), st));
+      k_chol_diag<T><<<(unsigned)dg.size(), 256, 0, st>>>(ddev, base, zbase, scratch, status);
+      AMB_LAUNCHED();
+      if (!panel.empty())
+        gemm_batched<T>(st, ring, panel, G_TRANS_B | G_TRI_B_UPPER, T(1), T(0), base, scratch, base);
     }
-    if (dg.empty()) break;
-    const DiagDesc* ddev = static_cast<const DiagDesc*>(ring.push(dg.data(), dg.size() * sizeof(DiagDesc), st));
-    k_chol_diag<T><<<(unsigned)dg.size(), 256, 0, st>>>(ddev, base, zbase, scratch, status);
-    AMB_LAUNCHED();
-    if (!panel.empty()) {
-      gemm_batched<T>(st, ring, panel, G_TRANS_B | G_TRI_B_UPPER, T(1), T(0), base, scratch, base);
-      gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
+    // trailing update with the whole outer block: C(lower) -= P P^T
+    std::vector<GemmDesc> trail;
+    for (const auto& x : d) {
+      const int J0 = x.c0 + ob * kOuter;
+      if (J0 >= x.c1) continue;
+      const int J1 = std::min(J0 + kOuter, x.c1);
+      const int rem = x.n - J1;
+      if (rem <= 0) continue;
+      trail.push_back(GemmDesc{rem, rem, J1 - J0, x.ld, x.ld, x.ld, x.off + J1 + (int64_t)J0 * x.ld,
+                               x.off + J1 + (int64_t)J0 * x.ld, x.off + J1 + (int64_t)J1 * x.ld});
+      if (flops) *flops += (double)rem * (rem + 1) * (J1 - J0);
     }
+    if (!trail.empty()) gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
   }
 }
 
