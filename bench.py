@@ -129,8 +129,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2block"],
-                    help="c2: the 48^3 workload; c2block: its 2x1x1 corner block (two of its substructures, "
-                         "same shapes, ~0.5 GB on the device), for profiler captures")
+                    help="c2: the 48^3 workload; c2block: a corner block of its substructures (same shapes; "
+                         "2x1x1 holds ~0.5 GB on the device), for profiler captures")
+    ap.add_argument("--block", default="2,1,1", help="substructures per axis of the c2block workload")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, family timing, Schur sweep or baselines)")
     args = ap.parse_args()
@@ -140,7 +141,7 @@ def main():
     prob = ai.config(2)
     workload = WORKLOAD
     if args.workload == "c2block":
-        prob = ai.sub_block(prob, (2, 1, 1))
+        prob = ai.sub_block(prob, tuple(int(v) for v in args.block.split(",")))
         workload = prob.name
 
     if args.impl == "reference":

@@ -255,6 +255,24 @@ __global__ void k_lob_zero(T* base, const int64_t* qp, int which, int c0, int w)
   base[QP(p, which) + c0 * N + idx] = T(0);
 }
 
+// S_ff of both sides of each pair: the rows and columns of S^(s) (S^(t)) at
+// the shared positions ps (pt), column-major nf x nf.  One CTA per (column,
+// pair side); grid.x = 2 x pairs, grid.y covers the largest nf.
+template <typename T>
+__global__ void k_lob_sff(T* Sff, const T* S, const int64_t* qp, const int64_t* soff, const int32_t* ps,
+                          const int32_t* pt) {
+  const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
+  const int64_t nf = QP(p, Q_NF);
+  const int64_t b = blockIdx.y;
+  if (b >= nf) return;
+  const int sub = (int)(side ? QP(p, Q_T) : QP(p, Q_S));
+  const int64_t ng = side ? QP(p, Q_NT) : QP(p, Q_NS);
+  const int32_t* pos = (side ? pt : ps) + QP(p, Q_FOFF);
+  const T* src = S + soff[sub] + (int64_t)pos[b] * ng;
+  T* dst = Sff + QP(p, Q_OF) + side * nf * nf + b * nf;
+  for (int64_t a = threadIdx.x; a < nf; a += blockDim.x) dst[a] = src[pos[a]];
+}
+
 // coarse gather/scatter of the pair coarse space
 template <typename T>
 __global__ void k_lob_cgather(T* C, const int64_t* qp, int m, const int32_t* cms, const int32_t* cmt) {
@@ -777,29 +795,19 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const T one = T(1), zero = T(0);
   std::vector<int> active(np, 1), iters(np, 0), conv(np, 0);
 
-  // S_ff of each side (gathered once)
+  // S_ff of each side (gathered once, on the device)
   {
-    std::vector<int64_t> so, sv;   // destination offset, source offset
-    for (int p = 0; p < np; ++p) {
-      const PairTopo& P = tp.pairs[p];
-      const int64_t nf = (int64_t)P.ps.size();
-      for (int side = 0; side < 2; ++side) {
-        const int sub = side ? P.t : P.s;
-        const auto& pos = side ? P.pt : P.ps;
-        for (int64_t b = 0; b < nf; ++b)
-          for (int64_t a = 0; a < nf; ++a) {
-            so.push_back(qp[(size_t)p * Q_NPAIRF + Q_OF] + side * nf * nf + a + b * nf);
-            sv.push_back(L.pS.off[sub] + pos[a] + (int64_t)pos[b] * L.ng[sub]);
-          }
-      }
+    int64_t maxnf0 = 0;
+    for (int p = 0; p < np; ++p) maxnf0 = std::max(maxnf0, qp[(size_t)p * Q_NPAIRF + Q_NF]);
+    DevBuf dsoff;
+    upload(dsoff, L.pS.off, st);
+    if (maxnf0 > 0) {
+      AMB_CHECK(maxnf0 < 65536, AMB_EINVAL, "pair face larger than 65535 dofs");
+      k_lob_sff<T><<<dim3(2 * np, (unsigned)maxnf0), 128, 0, st>>>(dptr<T>(Sff), dptr<T>(L.S), QPd, dptr<int64_t>(dsoff),
+                                                                 dptr<int32_t>(dps), dptr<int32_t>(dpt));
+      AMB_LAUNCHED();
     }
-    DevBuf dso, dsv, tmpv;
-    upload(dso, so, st);
-    upload(dsv, sv, st);
-    tmpv.alloc(so.size() * sizeof(T));
-    gather<T, T>(st, dptr<T>(tmpv), dptr<T>(L.S), dptr<int64_t>(dsv), (int64_t)so.size());
-    scatter<T, T>(st, dptr<T>(Sff), dptr<T>(tmpv), dptr<int64_t>(dso), (int64_t)so.size());
-    AMB_CUDA(cudaStreamSynchronize(st));
+    AMB_CUDA(cudaStreamSynchronize(st));   // keep the offset table alive until the kernel ran
   }
   // pseudo-inverse of the pair coarse matrices (initial constraints)
   {
