@@ -139,30 +139,48 @@ void Engine<T>::assemble(LevelData<T>& L, const LevelData<T>* prev, const std::v
   if (!prev) {
     assemble_level1<T>(st, dptr<T>(L.M), dptr<int64_t>(off), dptr<int32_t>(n), dptr<int32_t>(mesh.elem_sub),
                        dptr<int32_t>(mesh.elem_local), dptr<double>(mesh.coeff), dptr<double>(mesh.khat), 8 * mesh.dpn,
-                       mesh.nel);
+                       mesh.nx, mesh.ny, mesh.nz);
   } else {
     const int nch = prev->ns;
     std::vector<int32_t> parent(cfg.parents[L.level - 2].begin(), cfg.parents[L.level - 2].end());
-    std::vector<int64_t> loc_off(nch), ent_off(nch + 1, 0);
+    std::vector<int64_t> loc_off(nch);
     std::vector<int32_t> nc32(nch);
     int64_t lo = 0;
     for (int s = 0; s < nch; ++s) {
       loc_off[s] = lo;
       lo += prev->nc[s];
       nc32[s] = prev->nc[s];
-      ent_off[s + 1] = ent_off[s] + (int64_t)prev->nc[s] * prev->nc[s];
     }
-    DevBuf dpar, dacoff, dnc, dlocoff, dloc, dent;
+    // children ordered by (rank among their siblings, index): pass r adds
+    // the r-th child of every parent
+    std::vector<int> rank(nch), seen(L.ns, 0);
+    int nrank = 0;
+    for (int s = 0; s < nch; ++s) {
+      rank[s] = seen[parent[s]]++;
+      nrank = std::max(nrank, rank[s] + 1);
+    }
+    std::vector<int> pass_beg(nrank + 1, 0);
+    for (int s = 0; s < nch; ++s) ++pass_beg[rank[s] + 1];
+    for (int r = 0; r < nrank; ++r) pass_beg[r + 1] += pass_beg[r];
+    std::vector<int32_t> child(nch);
+    {
+      std::vector<int> cur(pass_beg.begin(), pass_beg.end() - 1);
+      for (int s = 0; s < nch; ++s) child[cur[rank[s]]++] = s;
+    }
+    std::vector<int64_t> ent_off(nch + 1, 0);
+    for (int q = 0; q < nch; ++q) ent_off[q + 1] = ent_off[q] + (int64_t)nc32[child[q]] * nc32[child[q]];
+    DevBuf dpar, dacoff, dnc, dlocoff, dloc, dent, dchild;
     upload(dpar, parent, st);
     upload(dacoff, prev->pAc.off, st);
     upload(dnc, nc32, st);
     upload(dlocoff, loc_off, st);
     upload(dloc, loc, st);
     upload(dent, ent_off, st);
+    upload(dchild, child, st);
     assemble_next<T>(st, dptr<T>(L.M), dptr<int64_t>(off), dptr<int32_t>(n), dptr<int32_t>(dpar), dptr<int64_t>(dacoff),
                      dptr<int32_t>(dnc), dptr<int64_t>(dlocoff), dptr<int32_t>(dloc), dptr<double>(prev->Ac),
-                     dptr<int64_t>(dent), nch, ent_off[nch]);
-    AMB_CUDA(cudaStreamSynchronize(st));   // keep the temporaries alive until the kernel ran
+                     dptr<int32_t>(dchild), dptr<int64_t>(dent), pass_beg, ent_off);
+    AMB_CUDA(cudaStreamSynchronize(st));   // keep the temporaries alive until the kernels ran
   }
   AMB_CUDA(cudaStreamSynchronize(st));
 }
@@ -382,7 +400,7 @@ void Engine<T>::setup_top() {
   LinvC.alloc((size_t)nC * nC * sizeof(double));
   topT.alloc((size_t)nC * sizeof(double));
   AMB_CUDA(cudaMemsetAsync(AC.p, 0, (size_t)nC * nC * sizeof(double), st));
-  top_assemble(st, dptr<double>(AC), nC, dptr<double>(L.Ac), dptr<int64_t>(L.rc), dptr<int64_t>(L.par), L.ns, imax(L.nc));
+  top_assemble(st, dptr<double>(AC), nC, dptr<double>(L.Ac), dptr<int64_t>(L.rc), dptr<int64_t>(L.par), L.nc);
   std::vector<CholDesc> d{CholDesc{0, (int32_t)nC, (int32_t)nC, 0, (int32_t)nC, 0, (int32_t)nC, -1}};
   double fl = 0;
   partial_cholesky<double>(st, ring, d, dptr<double>(AC), dptr<double>(LinvC), dptr<int>(status), &fl);

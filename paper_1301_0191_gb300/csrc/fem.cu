@@ -56,75 +56,100 @@ void compute_khat(cudaStream_t st, double* khat, int dpn, double h, double nu) {
   AMB_LAUNCHED();
 }
 
-// Level-1 assembly: every entry of every element matrix added into its
-// substructure's dense matrix (column-major, order n_s).
+// Level-1 assembly without atomics.  The elements are split into 8 colours
+// by the parities of their grid coordinates; two elements of one colour share
+// no node, so one colour pass adds to every entry of a substructure matrix
+// (column-major, order n_s) at most once, and the passes run in a fixed
+// order: the sums are the same on every run.
 template <typename T>
 __global__ void k_assemble1(T* M, const int64_t* sub_off, const int32_t* sub_n, const int32_t* elem_sub,
-                            const int32_t* elem_local, const double* coeff, const double* khat, int nd,
-                            int64_t nel) {
+                            const int32_t* elem_local, const double* coeff, const double* khat, int nd, int nx,
+                            int ny, int cx, int cy, int cz, int64_t hx, int64_t hy, int64_t ncol) {
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t per = (int64_t)nd * nd;
-  if (idx >= nel * per) return;
-  const int64_t e = idx / per;
+  if (idx >= ncol * per) return;
+  const int64_t q = idx / per;
   const int rc = (int)(idx % per);
+  const int64_t i = 2 * (q % hx) + cx, j = 2 * ((q / hx) % hy) + cy, k = 2 * (q / (hx * hy)) + cz;
+  const int64_t e = i + nx * (j + (int64_t)ny * k);
   const int a = rc % nd, b = rc / nd;
   const int la = elem_local[e * nd + a], lb = elem_local[e * nd + b];
   if (la < 0 || lb < 0) return;
   const int s = elem_sub[e];
   const int64_t n = sub_n[s];
-  atomicAdd(&M[sub_off[s] + la + lb * n], (T)(coeff[e] * khat[a + b * nd]));
+  T* dst = &M[sub_off[s] + la + lb * n];
+  *dst += (T)(coeff[e] * khat[a + b * nd]);
 }
 
 template <typename T>
 void assemble_level1(cudaStream_t st, T* M, const int64_t* sub_off, const int32_t* sub_n, const int32_t* elem_sub,
-                     const int32_t* elem_local, const double* coeff, const double* khat, int nd, int64_t nel) {
-  const int64_t total = nel * nd * nd;
-  k_assemble1<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M, sub_off, sub_n, elem_sub, elem_local, coeff,
-                                                                   khat, nd, nel);
-  AMB_LAUNCHED();
+                     const int32_t* elem_local, const double* coeff, const double* khat, int nd, int nx, int ny,
+                     int nz) {
+  for (int c = 0; c < 8; ++c) {
+    const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+    const int64_t hx = (nx - cx + 1) / 2, hy = (ny - cy + 1) / 2, hz = (nz - cz + 1) / 2;
+    const int64_t ncol = hx * hy * hz;
+    if (ncol <= 0) continue;
+    const int64_t total = ncol * nd * nd;
+    k_assemble1<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M, sub_off, sub_n, elem_sub, elem_local, coeff,
+                                                                     khat, nd, nx, ny, cx, cy, cz, hx, hy, ncol);
+    AMB_LAUNCHED();
+  }
 }
 
-// Level >= 2: child s contributes its coarse matrix (FP64, order nc_s).
+// Level >= 2: child s contributes its coarse matrix (FP64, order nc_s).  One
+// pass per sibling rank: the children of one pass have distinct parents, so
+// no entry is written twice within a pass, and the passes run in rank order.
+// child[0..nlist) lists the pass's children, ent_off[0..nlist] the running
+// entry offsets of their coarse matrices.
 template <typename T>
 __global__ void k_assemble_next(T* M, const int64_t* par_off, const int32_t* par_n, const int32_t* parent,
                                 const int64_t* ac_off, const int32_t* nc, const int64_t* loc_off,
-                                const int32_t* loc, const double* ac, const int64_t* ent_off, int nchild) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= ent_off[nchild]) return;
-  int lo = 0, hi = nchild - 1;
+                                const int32_t* loc, const double* ac, const int32_t* child, const int64_t* ent_off,
+                                int nlist) {
+  const int64_t idx = ent_off[0] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ent_off[nlist]) return;
+  int lo = 0, hi = nlist - 1;
   while (lo < hi) {
     int mid = (lo + hi + 1) >> 1;
     if (ent_off[mid] <= idx) lo = mid; else hi = mid - 1;
   }
-  const int s = lo;
-  const int64_t r = idx - ent_off[s];
+  const int s = child[lo];
+  const int64_t r = idx - ent_off[lo];
   const int n = nc[s];
   const int a = (int)(r % n), b = (int)(r / n);
   const int la = loc[loc_off[s] + a], lb = loc[loc_off[s] + b];
   const int P = parent[s];
-  atomicAdd(&M[par_off[P] + la + (int64_t)lb * par_n[P]], (T)ac[ac_off[s] + a + (int64_t)b * n]);
+  M[par_off[P] + la + (int64_t)lb * par_n[P]] += (T)ac[ac_off[s] + a + (int64_t)b * n];
 }
 
 template <typename T>
 void assemble_next(cudaStream_t st, T* M, const int64_t* par_off, const int32_t* par_n, const int32_t* parent,
                    const int64_t* ac_off, const int32_t* nc, const int64_t* loc_off, const int32_t* loc,
-                   const double* ac, const int64_t* ent_off, int nchild, int64_t total) {
-  if (total == 0) return;
-  k_assemble_next<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M, par_off, par_n, parent, ac_off, nc, loc_off,
-                                                                     loc, ac, ent_off, nchild);
-  AMB_LAUNCHED();
+                   const double* ac, const int32_t* child, const int64_t* ent_off, const std::vector<int>& pass_beg,
+                   const std::vector<int64_t>& ent_h) {
+  for (size_t r = 0; r + 1 < pass_beg.size(); ++r) {
+    const int b = pass_beg[r], e = pass_beg[r + 1];
+    const int64_t total = ent_h[e] - ent_h[b];
+    if (total <= 0) continue;
+    k_assemble_next<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(M, par_off, par_n, parent, ac_off, nc, loc_off,
+                                                                       loc, ac, child + b, ent_off + b, e - b);
+    AMB_LAUNCHED();
+  }
 }
 
 template void assemble_level1<float>(cudaStream_t, float*, const int64_t*, const int32_t*, const int32_t*,
-                                     const int32_t*, const double*, const double*, int, int64_t);
+                                     const int32_t*, const double*, const double*, int, int, int, int);
 template void assemble_level1<double>(cudaStream_t, double*, const int64_t*, const int32_t*, const int32_t*,
-                                      const int32_t*, const double*, const double*, int, int64_t);
+                                      const int32_t*, const double*, const double*, int, int, int, int);
 template void assemble_next<float>(cudaStream_t, float*, const int64_t*, const int32_t*, const int32_t*,
                                    const int64_t*, const int32_t*, const int64_t*, const int32_t*, const double*,
-                                   const int64_t*, int, int64_t);
+                                   const int32_t*, const int64_t*, const std::vector<int>&,
+                                   const std::vector<int64_t>&);
 template void assemble_next<double>(cudaStream_t, double*, const int64_t*, const int32_t*, const int32_t*,
                                     const int64_t*, const int32_t*, const int64_t*, const int32_t*, const double*,
-                                    const int64_t*, int, int64_t);
+                                    const int32_t*, const int64_t*, const std::vector<int>&,
+                                    const std::vector<int64_t>&);
 
 // y = A x on full-grid nodal vectors, one thread per node: the node's rows
 // of the (up to 8) element matrices around it.  Dirichlet rows are zero

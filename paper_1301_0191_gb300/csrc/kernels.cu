@@ -412,20 +412,24 @@ void tridiag_extremes(cudaStream_t st, double* out, const double* alphas, const 
   AMB_LAUNCHED();
 }
 
-__global__ void k_top_assemble(double* AC, int64_t nC, const double* Ac, const int64_t* rc, const int64_t* par) {
-  const int s = blockIdx.y;
+// Top coarse matrix: one launch per substructure, in order.  The coarse ids
+// of one substructure are distinct, so a launch writes each entry at most
+// once and the sums are formed in the same order on every run.
+__global__ void k_top_assemble(double* AC, int64_t nC, const double* Ac, const int64_t* rc, const int64_t* par, int s) {
   const int64_t nc = PAR(s, P_NC);
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nc * nc) return;
   const int64_t r = idx % nc, c = idx / nc;
   const int64_t base = PAR(s, P_VC);
-  atomicAdd(&AC[rc[base + r] + rc[base + c] * nC], Ac[PAR(s, P_OAC) + idx]);
+  AC[rc[base + r] + rc[base + c] * nC] += Ac[PAR(s, P_OAC) + idx];
 }
 void top_assemble(cudaStream_t st, double* AC, int64_t nC, const double* Ac, const int64_t* rc, const int64_t* par,
-                  int ns, int max_nc) {
-  if (ns <= 0 || max_nc <= 0) return;
-  k_top_assemble<<<dim3(blocks((int64_t)max_nc * max_nc), ns), 256, 0, st>>>(AC, nC, Ac, rc, par);
-  AMB_LAUNCHED();
+                  const std::vector<int>& nc) {
+  for (int s = 0; s < (int)nc.size(); ++s) {
+    if (nc[s] <= 0) continue;
+    k_top_assemble<<<blocks((int64_t)nc[s] * nc[s]), 256, 0, st>>>(AC, nC, Ac, rc, par, s);
+    AMB_LAUNCHED();
+  }
 }
 
 }  // namespace amb

@@ -3,6 +3,8 @@
 // scaling), per-substructure copies, small dense inverses, reductions.
 #pragma once
 
+#include <vector>
+
 #include "common.h"
 
 namespace amb {
@@ -75,6 +77,6 @@ void tridiag_extremes(cudaStream_t st, double* out, const double* alphas, const 
 
 // dense top-level coarse matrix: atomic scatter of every substructure's Ac
 void top_assemble(cudaStream_t st, double* AC, int64_t nC, const double* Ac, const int64_t* rc, const int64_t* par,
-                  int ns, int max_nc);
+                  const std::vector<int>& nc);
 
 }  // namespace amb

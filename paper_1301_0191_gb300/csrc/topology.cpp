@@ -1,10 +1,15 @@
 // Host-side substructuring (Sec. 2, Sec. 3, Sec. 7.1).  See topology.h.
+//
+// Every lookup from a level dof to a position runs through dense scratch
+// arrays over the level's dof space and every grouping through a sort, so
+// the cost is linear (up to sorts) in the mesh and interface sizes.
 #include "topology.h"
 
 #include <algorithm>
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 
 #include "amb.h"
 #include "common.h"
@@ -15,78 +20,136 @@ namespace {
 
 enum { TAG_X0 = 1, TAG_X1 = 2, TAG_Y0 = 4, TAG_Y1 = 8, TAG_Z0 = 16, TAG_Z1 = 32 };
 
+// Nodes of a level (level 1: mesh nodes; level >= 2: coarse objects of the
+// level below), in CSR form.
+struct LevelNodes {
+  int64_t n_dofs = 0;                         // level dof id space
+  std::vector<int> soff{0}, subs;             // sharing substructures of each node, sorted
+  std::vector<int> tags;                      // boundary bits of each node
+  std::vector<char> eligible;                 // may be a corner
+  std::vector<int64_t> doff{0}, dofs;         // level dofs of each node (none: no free dof)
+  std::vector<int> comps;                     // component of each of those dofs (-1 scalar)
+  int size() const { return (int)tags.size(); }
+  int nsub(int i) const { return soff[i + 1] - soff[i]; }
+  const int* sub(int i) const { return subs.data() + soff[i]; }
+  int64_t ndof(int i) const { return doff[i + 1] - doff[i]; }
+};
+
+bool set_less(const LevelNodes& N, int a, int b) {
+  return std::lexicographical_compare(N.sub(a), N.sub(a) + N.nsub(a), N.sub(b), N.sub(b) + N.nsub(b));
+}
+bool set_equal(const LevelNodes& N, int a, int b) {
+  return N.nsub(a) == N.nsub(b) && std::equal(N.sub(a), N.sub(a) + N.nsub(a), N.sub(b));
+}
+
 // Classify the nodes of a level and build its substructures, objects and
-// interface numbering.  node_elems_subs: per node its sharing set.
+// interface numbering.
 void classify(LevelTopo& L, const LevelNodes& N, int initial) {
-  const int nn = (int)N.subs.size();
+  const int nn = N.size();
   std::vector<char> iface(nn, 0), corner(nn, 0);
-  for (int i = 0; i < nn; ++i) iface[i] = N.subs[i].size() >= 2 && !N.dofs[i].empty();
+  std::vector<int> order;
+  for (int i = 0; i < nn; ++i) {
+    iface[i] = N.nsub(i) >= 2 && N.ndof(i) > 0;
+    if (iface[i]) order.push_back(i);
+  }
+  // rank of each interface node's sharing set in lexicographic set order:
+  // distinct sets by hashing, then only the distinct sets are sorted
+  std::vector<int> rank(nn, -1);
+  {
+    std::unordered_map<uint64_t, std::vector<int>> buckets;   // hash -> distinct set ids
+    std::vector<int> rep, sid(nn, -1);                         // representative node of each set
+    for (int i : order) {
+      uint64_t h = 1469598103934665603ull;
+      for (int k = 0; k < N.nsub(i); ++k) h = (h ^ (uint64_t)(uint32_t)N.sub(i)[k]) * 1099511628211ull;
+      auto& b = buckets[h];
+      int id = -1;
+      for (int r : b)
+        if (set_equal(N, rep[r], i)) { id = r; break; }
+      if (id < 0) {
+        id = (int)rep.size();
+        rep.push_back(i);
+        b.push_back(id);
+      }
+      sid[i] = id;
+    }
+    std::vector<int> ord(rep.size()), rk(rep.size());
+    for (size_t r = 0; r < rep.size(); ++r) ord[r] = (int)r;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return set_less(N, rep[a], rep[b]); });
+    for (size_t r = 0; r < ord.size(); ++r) rk[ord[r]] = (int)r;
+    for (int i : order) rank[i] = rk[sid[i]];
+  }
   // corner rule: alone in its (sharing set, tags) class
-  std::map<std::vector<int>, int> cls;
-  auto key_of = [&](int i) {
-    std::vector<int> k = N.subs[i];
-    k.push_back(-1 - N.tags[i]);
-    return k;
-  };
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    if (rank[a] != rank[b]) return rank[a] < rank[b];
+    return N.tags[a] != N.tags[b] ? N.tags[a] < N.tags[b] : a < b;
+  });
+  for (size_t r = 0; r < order.size();) {
+    size_t e = r + 1;
+    while (e < order.size() && rank[order[r]] == rank[order[e]] && N.tags[order[r]] == N.tags[order[e]]) ++e;
+    if (e == r + 1 && N.eligible[order[r]]) corner[order[r]] = 1;
+    r = e;
+  }
+  // remaining interface nodes grouped by sharing set: sets in lexicographic
+  // order, nodes in index order within a set
+  std::vector<int> grp;
   for (int i = 0; i < nn; ++i)
-    if (iface[i]) cls[key_of(i)] += 1;
-  for (int i = 0; i < nn; ++i)
-    if (iface[i] && N.eligible[i] && cls[key_of(i)] == 1) corner[i] = 1;
-  std::map<std::vector<int>, std::vector<int>> groups;
-  for (int i = 0; i < nn; ++i)
-    if (iface[i] && !corner[i]) groups[N.subs[i]].push_back(i);
+    if (iface[i] && !corner[i]) grp.push_back(i);
+  std::stable_sort(grp.begin(), grp.end(), [&](int a, int b) { return rank[a] < rank[b]; });
 
   L.n_dofs = N.n_dofs;
   L.objs.clear();
   // corner objects, in node order
-  std::vector<int> corner_obj(nn, -1);
   for (int i = 0; i < nn; ++i) {
     if (!corner[i]) continue;
     CoarseObj ob;
     ob.kind = OBJ_CORNER;
-    ob.subs = N.subs[i];
+    ob.subs.assign(N.sub(i), N.sub(i) + N.nsub(i));
     ob.tags = N.tags[i];
     ob.corner_node = i;
-    for (size_t q = 0; q < N.dofs[i].size(); ++q) {
-      ob.comps.push_back(N.comps[i][q]);
-      ob.dofs.push_back({N.dofs[i][q]});
+    for (int64_t q = N.doff[i]; q < N.doff[i + 1]; ++q) {
+      ob.comps.push_back(N.comps[q]);
+      ob.dofs.push_back({N.dofs[q]});
       ob.w.push_back({1.0});
     }
-    corner_obj[i] = (int)L.objs.size();
     L.objs.push_back(std::move(ob));
   }
   L.n_corner_nodes = (int)L.objs.size();
-  // edges (sets of >= 3 substructures), in key order
+  // edges (sets of >= 3 substructures) in set order; faces (2 substructures)
   L.n_edges = 0;
-  L.n_faces = 0;
-  std::vector<std::pair<std::vector<int>, std::vector<int>>> faces;
-  for (auto& kv : groups) {
-    if (kv.first.size() == 2) {
-      faces.push_back(kv);
-      continue;
-    }
-    ++L.n_edges;
-    if (initial != AMB_CORNERS_EDGES) continue;
-    CoarseObj ob;
-    ob.kind = OBJ_EDGE;
-    ob.subs = kv.first;
-    int tags = ~0;
-    std::map<int, std::vector<int64_t>> bycomp;
-    for (int i : kv.second) {
-      tags &= N.tags[i];
-      for (size_t q = 0; q < N.dofs[i].size(); ++q) {
-        AMB_CHECK(N.comps[i][q] >= 0, AMB_EINVAL, "a scalar coarse dof lies on an edge of the next level");
-        bycomp[N.comps[i][q]].push_back(N.dofs[i][q]);
+  std::vector<std::pair<int, std::vector<int>>> faces;   // (first node of the set, nodes)
+  for (size_t r = 0; r < grp.size();) {
+    size_t e = r + 1;
+    while (e < grp.size() && rank[grp[r]] == rank[grp[e]]) ++e;
+    const int i0 = grp[r];
+    if (N.nsub(i0) == 2) {
+      faces.emplace_back(i0, std::vector<int>(grp.begin() + r, grp.begin() + e));
+    } else {
+      ++L.n_edges;
+      if (initial == AMB_CORNERS_EDGES) {
+        CoarseObj ob;
+        ob.kind = OBJ_EDGE;
+        ob.subs.assign(N.sub(i0), N.sub(i0) + N.nsub(i0));
+        int tags = ~0;
+        std::map<int, std::vector<int64_t>> bycomp;
+        for (size_t g = r; g < e; ++g) {
+          const int i = grp[g];
+          tags &= N.tags[i];
+          for (int64_t q = N.doff[i]; q < N.doff[i + 1]; ++q) {
+            AMB_CHECK(N.comps[q] >= 0, AMB_EINVAL, "a scalar coarse dof lies on an edge of the next level");
+            bycomp[N.comps[q]].push_back(N.dofs[q]);
+          }
+        }
+        ob.tags = tags;
+        for (auto& c : bycomp) {
+          std::sort(c.second.begin(), c.second.end());
+          ob.comps.push_back(c.first);
+          ob.w.push_back(std::vector<double>(c.second.size(), 1.0 / (double)c.second.size()));
+          ob.dofs.push_back(c.second);
+        }
+        L.objs.push_back(std::move(ob));
       }
     }
-    ob.tags = tags;
-    for (auto& c : bycomp) {
-      std::sort(c.second.begin(), c.second.end());
-      ob.comps.push_back(c.first);
-      ob.w.push_back(std::vector<double>(c.second.size(), 1.0 / (double)c.second.size()));
-      ob.dofs.push_back(c.second);
-    }
-    L.objs.push_back(std::move(ob));
+    r = e;
   }
   L.n_faces = (int)faces.size();
 
@@ -94,16 +157,16 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
   L.subs.assign(L.n_subs, SubTopo());
   std::vector<std::vector<int64_t>> inter(L.n_subs), delta(L.n_subs), crn(L.n_subs);
   for (int i = 0; i < nn; ++i) {
-    if (N.dofs[i].empty()) continue;
-    for (int s : N.subs[i]) {
+    if (N.ndof(i) == 0) continue;
+    for (int k = 0; k < N.nsub(i); ++k) {
+      const int s = N.sub(i)[k];
       auto& dst = !iface[i] ? inter[s] : (corner[i] ? crn[s] : delta[s]);
-      for (int64_t d : N.dofs[i]) dst.push_back(d);
+      dst.insert(dst.end(), N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1]);
     }
   }
   L.corner_dofs.clear();
   for (int i = 0; i < nn; ++i)
-    if (corner[i])
-      for (int64_t d : N.dofs[i]) L.corner_dofs.push_back(d);
+    if (corner[i]) L.corner_dofs.insert(L.corner_dofs.end(), N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1]);
   std::sort(L.corner_dofs.begin(), L.corner_dofs.end());
   for (int s = 0; s < L.n_subs; ++s) {
     std::sort(inter[s].begin(), inter[s].end());
@@ -113,41 +176,50 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
     sb.n_i = (int)inter[s].size();
     sb.n_g = (int)(delta[s].size() + crn[s].size());
     sb.n_crn = (int)crn[s].size();
+    sb.dofs.reserve(inter[s].size() + sb.n_g);
     sb.dofs = inter[s];
     sb.dofs.insert(sb.dofs.end(), delta[s].begin(), delta[s].end());
     sb.dofs.insert(sb.dofs.end(), crn[s].begin(), crn[s].end());
   }
-  // global interface numbering and owners
-  std::map<int64_t, std::vector<std::pair<int, int>>> own;
-  L.gidx.assign(L.n_subs, {});
+  // global interface numbering (increasing level dof) and owners (increasing
+  // substructure), by counting over the level's dof space
+  std::vector<int> cnt(N.n_dofs + 1, 0);
   for (int s = 0; s < L.n_subs; ++s) {
     const SubTopo& sb = L.subs[s];
-    for (int l = 0; l < sb.n_g; ++l) own[sb.dofs[sb.n_i + l]].push_back({s, l});
+    for (int l = 0; l < sb.n_g; ++l) ++cnt[sb.dofs[sb.n_i + l]];
   }
   L.iface_dofs.clear();
   L.own_off.assign(1, 0);
-  L.own_sub.clear();
-  L.own_pos.clear();
-  for (int s = 0; s < L.n_subs; ++s) L.gidx[s].assign(L.subs[s].n_g, -1);
-  for (auto& kv : own) {
-    int j = (int)L.iface_dofs.size();
-    L.iface_dofs.push_back(kv.first);
-    for (auto& sp : kv.second) {
-      L.own_sub.push_back(sp.first);
-      L.own_pos.push_back(sp.second);
-      L.gidx[sp.first][sp.second] = j;
+  std::vector<int> slot(N.n_dofs, -1);   // level dof -> global interface index
+  for (int64_t d = 0; d < N.n_dofs; ++d) {
+    if (cnt[d] == 0) continue;
+    slot[d] = (int)L.iface_dofs.size();
+    L.iface_dofs.push_back(d);
+    L.own_off.push_back(L.own_off.back() + cnt[d]);
+  }
+  L.own_sub.assign(L.own_off.back(), 0);
+  L.own_pos.assign(L.own_off.back(), 0);
+  std::vector<int> fill(L.iface_dofs.size(), 0);
+  L.gidx.assign(L.n_subs, {});
+  for (int s = 0; s < L.n_subs; ++s) {
+    const SubTopo& sb = L.subs[s];
+    L.gidx[s].assign(sb.n_g, -1);
+    for (int l = 0; l < sb.n_g; ++l) {
+      const int j = slot[sb.dofs[sb.n_i + l]];
+      const int q = L.own_off[j] + fill[j]++;
+      L.own_sub[q] = s;
+      L.own_pos[q] = l;
+      L.gidx[s][l] = j;
     }
-    L.own_off.push_back((int)L.own_sub.size());
   }
   // pairs: faces with at least one face-class dof, sorted by (s, t)
   L.pairs.clear();
   for (auto& f : faces) {
     PairTopo p;
-    p.s = f.first[0];
-    p.t = f.first[1];
+    p.s = N.sub(f.first)[0];
+    p.t = N.sub(f.first)[1];
     std::vector<int64_t> fd;
-    for (int i : f.second)
-      for (int64_t d : N.dofs[i]) fd.push_back(d);
+    for (int i : f.second) fd.insert(fd.end(), N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1]);
     if (fd.empty()) continue;
     std::sort(fd.begin(), fd.end());
     p.face_dofs = fd;
@@ -169,15 +241,16 @@ void number_coarse(LevelTopo& L) {
     n += (int64_t)ob.dofs.size();
   }
   L.n_coarse = n;
-  // object lists per substructure
+  // object lists per substructure (increasing object index)
   std::vector<std::vector<int>> objs_of(L.n_subs);
   for (int o = 0; o < (int)L.objs.size(); ++o)
     for (int s : L.objs[o].subs) objs_of[s].push_back(o);
+  // scratch over the level's dof space, reset after each use
+  std::vector<int> gpos(L.n_dofs, -1);
   for (int s = 0; s < L.n_subs; ++s) {
     SubTopo& sb = L.subs[s];
-    std::map<int64_t, int> gpos;   // level dof -> interface position
     for (int l = 0; l < sb.n_g; ++l) gpos[sb.dofs[sb.n_i + l]] = l;
-    std::map<int64_t, int64_t> corner_coarse;   // corner level dof -> coarse id
+    std::vector<int64_t> cc(sb.n_crn, -1);   // coarse id of each corner position
     sb.rc.clear();
     sb.crows.clear();
     std::vector<int64_t> others;
@@ -185,13 +258,14 @@ void number_coarse(LevelTopo& L) {
       const CoarseObj& ob = L.objs[o];
       for (size_t q = 0; q < ob.dofs.size(); ++q) {
         if (ob.kind == OBJ_CORNER) {
-          corner_coarse[ob.dofs[q][0]] = ob.first + (int64_t)q;
+          const int pos = gpos[ob.dofs[q][0]];
+          if (pos >= sb.n_d()) cc[pos - sb.n_d()] = ob.first + (int64_t)q;
         } else {
           std::vector<std::pair<int, double>> row;
+          row.reserve(ob.dofs[q].size());
           for (size_t e = 0; e < ob.dofs[q].size(); ++e) {
-            auto it = gpos.find(ob.dofs[q][e]);
-            AMB_CHECK(it != gpos.end(), AMB_EINVAL, "constraint dof outside the interface");
-            int pos = it->second;   // interface position
+            const int pos = gpos[ob.dofs[q][e]];
+            AMB_CHECK(pos >= 0, AMB_EINVAL, "constraint dof outside the interface");
             AMB_CHECK(pos < sb.n_d(), AMB_EINVAL, "non-corner constraint touches a corner dof");
             row.push_back({pos, ob.w[q][e]});
           }
@@ -200,53 +274,58 @@ void number_coarse(LevelTopo& L) {
         }
       }
     }
-    for (int l = sb.n_d(); l < sb.n_g; ++l) {
-      auto it = corner_coarse.find(sb.dofs[sb.n_i + l]);
-      AMB_CHECK(it != corner_coarse.end(), AMB_EINVAL, "corner dof without a coarse dof");
-      sb.rc.push_back(it->second);
+    for (int l = 0; l < sb.n_crn; ++l) {
+      AMB_CHECK(cc[l] >= 0, AMB_EINVAL, "corner dof without a coarse dof");
+      sb.rc.push_back(cc[l]);
     }
     sb.rc.insert(sb.rc.end(), others.begin(), others.end());
+    for (int l = 0; l < sb.n_g; ++l) gpos[sb.dofs[sb.n_i + l]] = -1;
   }
   // pair data
+  std::vector<int> pb(L.n_dofs, -1), fent(L.n_dofs, -1);
+  std::vector<std::pair<int64_t, int>> adofs;
   for (auto& p : L.pairs) {
     const SubTopo& a = L.subs[p.s];
     const SubTopo& b = L.subs[p.t];
-    std::map<int64_t, int> pa, pb;
-    for (int l = 0; l < a.n_g; ++l) pa[a.dofs[a.n_i + l]] = l;
     for (int l = 0; l < b.n_g; ++l) pb[b.dofs[b.n_i + l]] = l;
+    // shared positions in increasing level-dof order
+    adofs.clear();
+    for (int l = 0; l < a.n_g; ++l) adofs.push_back({a.dofs[a.n_i + l], l});
+    std::sort(adofs.begin(), adofs.end());
     p.ps.clear();
     p.pt.clear();
-    std::map<int64_t, int> fent;   // level dof -> entry index
-    for (auto& kv : pa) {
-      auto it = pb.find(kv.first);
-      if (it == pb.end()) continue;
-      fent[kv.first] = (int)p.ps.size();
-      p.ps.push_back(kv.second);
-      p.pt.push_back(it->second);
+    for (const auto& dl : adofs) {
+      const int lb = pb[dl.first];
+      if (lb < 0) continue;
+      fent[dl.first] = (int)p.ps.size();
+      p.ps.push_back(dl.second);
+      p.pt.push_back(lb);
     }
     p.face.clear();
     for (int64_t d : p.face_dofs) {
-      auto it = fent.find(d);
-      AMB_CHECK(it != fent.end(), AMB_EINVAL, "face dof not shared by the pair");
-      p.face.push_back(it->second);
+      AMB_CHECK(fent[d] >= 0, AMB_EINVAL, "face dof not shared by the pair");
+      p.face.push_back(fent[d]);
     }
-    // jump groups: initial objects (corners, edges) shared by both
+    // jump groups: initial objects (corners, edges) shared by both, in object order
     p.goff.assign(1, 0);
     p.gent.clear();
     p.gw.clear();
-    for (const auto& ob : L.objs) {
+    for (int o : objs_of[p.s]) {
+      const CoarseObj& ob = L.objs[o];
       if (ob.kind == OBJ_ADAPTIVE) continue;
-      if (!std::binary_search(ob.subs.begin(), ob.subs.end(), p.s) ||
-          !std::binary_search(ob.subs.begin(), ob.subs.end(), p.t))
-        continue;
+      if (!std::binary_search(ob.subs.begin(), ob.subs.end(), p.t)) continue;
       for (size_t q = 0; q < ob.dofs.size(); ++q) {
         for (size_t e = 0; e < ob.dofs[q].size(); ++e) {
-          p.gent.push_back(fent.at(ob.dofs[q][e]));
+          const int f = fent[ob.dofs[q][e]];
+          AMB_CHECK(f >= 0, AMB_EINVAL, "jump constraint dof not shared by the pair");
+          p.gent.push_back(f);
           p.gw.push_back(ob.w[q][e]);
         }
         p.goff.push_back((int)p.gent.size());
       }
     }
+    for (int l = 0; l < b.n_g; ++l) pb[b.dofs[b.n_i + l]] = -1;
+    for (const auto& dl : adofs) fent[dl.first] = -1;
     // pair coarse space (initial coarse dofs of both substructures)
     std::map<int64_t, int> pc;
     for (int64_t c : a.rc) pc.emplace(c, 0);
@@ -282,40 +361,52 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
   const int64_t nnx = nx + 1, nny = ny + 1, nnz = nz + 1;
   const int64_t nn = nnx * nny * nnz;
   const int64_t nel = (int64_t)nx * ny * nz;
+  for (int64_t e = 0; e < nel; ++e)
+    AMB_CHECK(elem_to_sub[e] >= 0 && elem_to_sub[e] < n_subs, AMB_EINVAL, "elem_to_sub out of range");
   LevelNodes N;
   N.n_dofs = nn * dpn;
-  N.subs.assign(nn, {});
   N.tags.assign(nn, 0);
   N.eligible.assign(nn, 1);
-  N.dofs.assign(nn, {});
-  N.comps.assign(nn, {});
-  for (int64_t e = 0; e < nel; ++e) {
-    const int s = elem_to_sub[e];
-    AMB_CHECK(s >= 0 && s < n_subs, AMB_EINVAL, "elem_to_sub out of range");
-    const int64_t i = e % nx, j = (e / nx) % ny, k = e / ((int64_t)nx * ny);
-    for (int a = 0; a < 8; ++a) {
-      const int64_t n = (i + (a & 1)) + nnx * ((j + ((a >> 1) & 1)) + nny * (k + ((a >> 2) & 1)));
-      auto& v = N.subs[n];
-      if (std::find(v.begin(), v.end(), s) == v.end()) v.push_back(s);
-    }
-  }
-  for (int64_t n = 0; n < nn; ++n) {
-    std::sort(N.subs[n].begin(), N.subs[n].end());
-    const int64_t i = n % nnx, j = (n / nnx) % nny, k = n / (nnx * nny);
-    int t = 0;
-    if (i == 0) t |= TAG_X0;
-    if (i == nx) t |= TAG_X1;
-    if (j == 0) t |= TAG_Y0;
-    if (j == ny) t |= TAG_Y1;
-    if (k == 0) t |= TAG_Z0;
-    if (k == nz) t |= TAG_Z1;
-    N.tags[n] = t;
-    if (!dirichlet[n])
-      for (int c = 0; c < dpn; ++c) {
-        N.dofs[n].push_back(n * dpn + c);
-        N.comps[n].push_back(c);
+  N.soff.reserve(nn + 1);
+  N.subs.reserve(nn + nn / 4);
+  N.doff.reserve(nn + 1);
+  N.dofs.reserve(nn * dpn);
+  N.comps.reserve(nn * dpn);
+  for (int64_t k = 0; k < nnz; ++k)
+    for (int64_t j = 0; j < nny; ++j)
+      for (int64_t i = 0; i < nnx; ++i) {
+        const int64_t n = i + nnx * (j + nny * k);
+        // sharing set: substructures of the (up to 8) elements around the node
+        int set[8], c = 0;
+        for (int64_t ek = k - 1; ek <= k; ++ek) {
+          if (ek < 0 || ek >= nz) continue;
+          for (int64_t ej = j - 1; ej <= j; ++ej) {
+            if (ej < 0 || ej >= ny) continue;
+            for (int64_t ei = i - 1; ei <= i; ++ei) {
+              if (ei < 0 || ei >= nx) continue;
+              const int s = elem_to_sub[ei + nx * (ej + ny * ek)];
+              if (std::find(set, set + c, s) == set + c) set[c++] = s;
+            }
+          }
+        }
+        std::sort(set, set + c);
+        N.subs.insert(N.subs.end(), set, set + c);
+        N.soff.push_back((int)N.subs.size());
+        int t = 0;
+        if (i == 0) t |= TAG_X0;
+        if (i == nx) t |= TAG_X1;
+        if (j == 0) t |= TAG_Y0;
+        if (j == ny) t |= TAG_Y1;
+        if (k == 0) t |= TAG_Z0;
+        if (k == nz) t |= TAG_Z1;
+        N.tags[n] = t;
+        if (!dirichlet[n])
+          for (int q = 0; q < dpn; ++q) {
+            N.dofs.push_back(n * dpn + q);
+            N.comps.push_back(q);
+          }
+        N.doff.push_back((int64_t)N.dofs.size());
       }
-  }
   LevelTopo L;
   L.n_subs = n_subs;
   classify(L, N, initial);
@@ -326,19 +417,23 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
   const int nd = 8 * dpn;
   elem_local.assign(nel * nd, -1);
   std::vector<int32_t> loc(nn * dpn, -1);
-  std::vector<std::vector<int64_t>> elems_of(n_subs);
-  for (int64_t e = 0; e < nel; ++e) elems_of[elem_to_sub[e]].push_back(e);
+  std::vector<int64_t> eoff(n_subs + 1, 0), elems(nel);
+  for (int64_t e = 0; e < nel; ++e) ++eoff[elem_to_sub[e] + 1];
+  for (int s = 0; s < n_subs; ++s) eoff[s + 1] += eoff[s];
+  {
+    std::vector<int64_t> cur(eoff.begin(), eoff.end() - 1);
+    for (int64_t e = 0; e < nel; ++e) elems[cur[elem_to_sub[e]]++] = e;
+  }
   for (int s = 0; s < n_subs; ++s) {
     const SubTopo& sb = L.subs[s];
     for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = (int32_t)q;
-    for (int64_t e : elems_of[s]) {
+    for (int64_t x = eoff[s]; x < eoff[s + 1]; ++x) {
+      const int64_t e = elems[x];
       const int64_t i = e % nx, j = (e / nx) % ny, k = e / ((int64_t)nx * ny);
       for (int a = 0; a < 8; ++a) {
         const int64_t n = (i + (a & 1)) + nnx * ((j + ((a >> 1) & 1)) + nny * (k + ((a >> 2) & 1)));
-        for (int c = 0; c < dpn; ++c) {
-          if (dirichlet[n]) continue;
-          elem_local[e * nd + a * dpn + c] = loc[n * dpn + c];
-        }
+        if (dirichlet[n]) continue;
+        for (int c = 0; c < dpn; ++c) elem_local[e * nd + a * dpn + c] = loc[n * dpn + c];
       }
     }
     for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = -1;
@@ -353,11 +448,8 @@ LevelTopo build_level_next(const LevelTopo& prev, const int32_t* parent, int n_s
   LevelNodes N;
   N.n_dofs = prev.n_coarse;
   const int no = (int)prev.objs.size();
-  N.subs.assign(no, {});
   N.tags.assign(no, 0);
   N.eligible.assign(no, 0);
-  N.dofs.assign(no, {});
-  N.comps.assign(no, {});
   for (int o = 0; o < no; ++o) {
     const CoarseObj& ob = prev.objs[o];
     std::vector<int> ps;
@@ -367,13 +459,15 @@ LevelTopo build_level_next(const LevelTopo& prev, const int32_t* parent, int n_s
     }
     std::sort(ps.begin(), ps.end());
     ps.erase(std::unique(ps.begin(), ps.end()), ps.end());
-    N.subs[o] = ps;
+    N.subs.insert(N.subs.end(), ps.begin(), ps.end());
+    N.soff.push_back((int)N.subs.size());
     N.tags[o] = ob.tags;
     N.eligible[o] = ob.kind == OBJ_CORNER;
     for (size_t q = 0; q < ob.dofs.size(); ++q) {
-      N.dofs[o].push_back(ob.first + (int64_t)q);
-      N.comps[o].push_back(ob.comps[q]);
+      N.dofs.push_back(ob.first + (int64_t)q);
+      N.comps.push_back(ob.comps[q]);
     }
+    N.doff.push_back((int64_t)N.dofs.size());
   }
   LevelTopo L;
   L.n_subs = n_subs;

@@ -31,16 +31,6 @@ struct CoarseObj {
   int corner_node = -1;                       // level node id of a corner
 };
 
-// Nodes of a level: level 1 = mesh nodes; level >= 2 = coarse objects of the level below.
-struct LevelNodes {
-  int64_t n_dofs = 0;                         // level dof id space
-  std::vector<std::vector<int>> subs;         // per node, sorted
-  std::vector<int> tags;                      // per node boundary bits
-  std::vector<char> eligible;                 // may be a corner
-  std::vector<std::vector<int64_t>> dofs;     // per node level dofs (empty: no free dof)
-  std::vector<std::vector<int>> comps;        // per node component of each dof
-};
-
 struct SubTopo {
   std::vector<int64_t> dofs;                  // [interior | delta | corner] level dof ids
   int n_i = 0, n_g = 0, n_crn = 0;            // n_delta = n_g - n_crn

@@ -155,6 +155,29 @@ def test_three_levels(B):
     ctx.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_runs_are_bitwise_reproducible(B, precision):
+    """Assembly, factorizations, LOBPCG and PCG use no atomics or
+    order-dependent reductions: two set-ups + solves of the same problem give
+    identical bits (two-level and three-level hierarchies)."""
+    prec = B.FP64 if precision == "fp64" else B.FP32
+    groups = [np.array([0, 2, 4]), np.array([0, 2]), np.array([0, 1])]
+    for prob in (ai.toy(4, 3, 17, split=(2, 2, 2), sigma=1.5, tau=3.0),
+                 ai.toy(3, 1, 41, split=(4, 2, 1), levels=3, groups=groups, sigma=1.0, tau=2.0)):
+        out = []
+        for _ in range(2):
+            c = _ctx(B, prob, precision=prec)
+            f = c.load_vector(prob.body)
+            u, info = c.solve(f)
+            rep = c.report()
+            out.append((u, info.iterations, [p["lam"] for p in rep["pairs"]], rep["n_adaptive"]))
+            c.close()
+        (u0, i0, l0, n0), (u1, i1, l1, n1) = out
+        assert i0 == i1 and n0 == n1
+        assert np.array_equal(u0, u1)
+        assert all(np.array_equal(np.asarray(a), np.asarray(b)) for a, b in zip(l0, l1))
+
+
 def test_fp32_preconditioner_reaches_fp64_tolerance(B):
     prob = ai.toy(4, 3, 15, split=(2, 2, 2), sigma=1.5, tau=3.0)
     c64 = _ctx(B, prob, lobpcg_tol=1e-8)
