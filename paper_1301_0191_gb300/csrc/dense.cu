@@ -396,9 +396,13 @@ template void gemm_batched<double, float>(cudaStream_t, DescRing&, const std::ve
                                           double, const float*, const double*, double*);
 
 // ------------------------------------------------------------------ GEMV
-// y = alpha op(A) x + beta y, one vector per descriptor.  No-transpose:
-// one thread per row, columns streamed (coalesced along rows); transpose:
-// one warp per output, lanes stride down the column.
+// y = alpha op(A) x + beta y, one vector per descriptor; every launch
+// streams its matrices from HBM once, so the kernels are built for bytes in
+// flight.  No-transpose: a CTA owns 32 rows (one per lane) and its warps take
+// interleaved 32-column chunks, each warp issuing its chunk's 32 column loads
+// back to back (x broadcast by shuffle); the warps' partial sums are merged
+// in a fixed order.  Transpose: one warp per output column, x staged in
+// shared memory, loads unrolled by 8.
 
 template <typename T>
 struct GemvArgs {
@@ -411,8 +415,10 @@ struct GemvArgs {
   T* Y;
 };
 
-constexpr int kGemvRows = 256;   // rows per CTA (no-transpose)
+constexpr int kGemvRows = 32;    // rows per CTA (no-transpose)
+constexpr int kGemvWarps = 8;    // warps per CTA
 constexpr int kGemvCols = 8;     // outputs per CTA (transpose): one warp each
+constexpr int kGemvXChunk = 2048;   // staged x entries (transpose)
 
 template <typename T>
 __device__ inline int gemv_find(const GemvArgs<T>& g, int bid) {
@@ -425,9 +431,9 @@ __device__ inline int gemv_find(const GemvArgs<T>& g, int bid) {
 }
 
 // Compensated accumulation for FP32 matrix-vector products: (hi, lo) holds
-// the running sum, products are split exactly by FMA and added by TwoSum.
-// The GEMVs stream their matrix from HBM, so the extra FP32 instructions
-// are hidden behind memory traffic.
+// the running sum, products are split exactly by FMA and added by TwoSum
+// (explicit _rn intrinsics: never contracted, so the transformations stay
+// exact).  The extra FP32 instructions hide behind the memory stream.
 struct DF {
   float hi = 0.f, lo = 0.f;
   __device__ __forceinline__ void add(float a, float b) {
@@ -446,128 +452,72 @@ struct DF {
     hi = s;
     lo = __fadd_rn(lo, __fadd_rn(er, o.lo));
   }
+  __device__ __forceinline__ void shfl_merge(int o) {
+    DF t;
+    t.hi = __shfl_xor_sync(0xffffffffu, hi, o);
+    t.lo = __shfl_xor_sync(0xffffffffu, lo, o);
+    merge(t);
+  }
   __device__ __forceinline__ float value() const { return __fadd_rn(hi, lo); }
 };
 
-__global__ void __launch_bounds__(kGemvRows) k_gemv_n_df(GemvArgs<float> g) {
-  __shared__ float xs[1024];
-  int lo_d = 0, hi_d = g.ndesc - 1;
-  while (lo_d < hi_d) {
-    int mid = (lo_d + hi_d + 1) >> 1;
-    if (g.prefix[mid] <= (int)blockIdx.x) lo_d = mid; else hi_d = mid - 1;
-  }
-  const GemvDesc d = g.desc[lo_d];
-  const int rb = blockIdx.x - g.prefix[lo_d];
-  const int i = rb * kGemvRows + threadIdx.x;
-  const float* __restrict__ A = g.A + d.a;
-  const float* __restrict__ x = g.X + d.x;
-  int lend = d.n;
-  if (g.flags & G_TRI_A_LOWER) lend = min(d.n, rb * kGemvRows + kGemvRows);
-  int lbeg = 0;
-  if (g.flags & G_TRI_A_UPPER) lbeg = rb * kGemvRows;
-  DF s0, s1;
-  for (int c0 = lbeg; c0 < lend; c0 += 1024) {
-    int cn = min(1024, lend - c0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < cn; q += kGemvRows) xs[q] = x[c0 + q];
-    __syncthreads();
-    if (i < d.m) {
-      int cl = 0, ch = cn;
-      if (g.flags & G_TRI_A_LOWER) ch = min(cn, i - c0 + 1);
-      if (g.flags & G_TRI_A_UPPER) cl = max(0, i - c0);
-      const float* col = A + i + (int64_t)(c0 + cl) * d.lda;
-      int q = cl;
-      for (; q + 1 < ch; q += 2) {
-        s0.add(col[0], xs[q]);
-        s1.add(col[d.lda], xs[q + 1]);
-        col += 2 * (int64_t)d.lda;
-      }
-      for (; q < ch; ++q) {
-        s0.add(col[0], xs[q]);
-        col += d.lda;
-      }
-    }
-  }
-  if (i < d.m) {
-    s0.merge(s1);
-    float v = g.alpha * s0.value();
-    float* y = g.Y + d.y;
-    if (g.beta != 0.f) v = fmaf(g.beta, y[i], v);
-    y[i] = v;
-  }
-}
+// Plain FP64 accumulation with the same interface.
+struct D64 {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ void merge(const D64& o) { v += o.v; }
+  __device__ __forceinline__ void shfl_merge(int o) { v += __shfl_xor_sync(0xffffffffu, v, o); }
+  __device__ __forceinline__ double value() const { return v; }
+};
 
-__global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t_df(GemvArgs<float> g) {
-  int lo_d = 0, hi_d = g.ndesc - 1;
-  while (lo_d < hi_d) {
-    int mid = (lo_d + hi_d + 1) >> 1;
-    if (g.prefix[mid] <= (int)blockIdx.x) lo_d = mid; else hi_d = mid - 1;
-  }
-  const GemvDesc d = g.desc[lo_d];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = (blockIdx.x - g.prefix[lo_d]) * kGemvCols + warp;
-  if (j >= d.n) return;
-  const float* __restrict__ col = g.A + d.a + (int64_t)j * d.lda;
-  const float* __restrict__ x = g.X + d.x;
-  int ib = 0, ie = d.m;
-  if (g.flags & G_TRI_A_UPPER) ib = min(j, d.m);
-  if (g.flags & G_TRI_A_LOWER) ie = min(d.m, j + 1);
-  DF s;
-  for (int i = ib + lane; i < ie; i += 32) s.add(col[i], x[i]);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    DF t;
-    t.hi = __shfl_xor_sync(0xffffffffu, s.hi, o);
-    t.lo = __shfl_xor_sync(0xffffffffu, s.lo, o);
-    s.merge(t);
-  }
-  if (lane == 0) {
-    float v = g.alpha * s.value();
-    float* y = g.Y + d.y;
-    if (g.beta != 0.f) v = fmaf(g.beta, y[j], v);
-    y[j] = v;
-  }
-}
+template <typename T> struct GemvAcc;
+template <> struct GemvAcc<float> { using type = DF; };
+template <> struct GemvAcc<double> { using type = D64; };
 
 template <typename T>
-__global__ void __launch_bounds__(kGemvRows) k_gemv_n(GemvArgs<T> g) {
-  __shared__ T xs[1024];
+__global__ void __launch_bounds__(32 * kGemvWarps) k_gemv_n(GemvArgs<T> g) {
+  using Acc = typename GemvAcc<T>::type;
+  __shared__ Acc red[kGemvWarps][32];
   const int di = gemv_find(g, blockIdx.x);
   const GemvDesc d = g.desc[di];
-  const int i = (blockIdx.x - g.prefix[di]) * kGemvRows + threadIdx.x;
-  const T* __restrict__ A = g.A + d.a;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = (blockIdx.x - g.prefix[di]) * kGemvRows, i = i0 + lane;
+  const bool row_ok = i < d.m;
+  const bool lower = g.flags & G_TRI_A_LOWER, upper = g.flags & G_TRI_A_UPPER;
+  int cbeg = 0, cend = d.n;
+  if (lower) cend = min(d.n, i0 + kGemvRows);
+  if (upper) cbeg = min(d.n, i0);
+  const T* __restrict__ A = g.A + d.a + (row_ok ? i : i0);
   const T* __restrict__ x = g.X + d.x;
-  int lend = d.n;
-  if (g.flags & G_TRI_A_LOWER) lend = min(d.n, (blockIdx.x - g.prefix[di]) * kGemvRows + kGemvRows);
-  int lbeg = 0;
-  if (g.flags & G_TRI_A_UPPER) lbeg = (blockIdx.x - g.prefix[di]) * kGemvRows;
-  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  for (int c0 = lbeg; c0 < lend; c0 += 1024) {
-    int cn = min(1024, lend - c0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < cn; q += kGemvRows) xs[q] = x[c0 + q];
-    __syncthreads();
-    if (i < d.m) {
-      int cl = 0, ch = cn;
-      if (g.flags & G_TRI_A_LOWER) ch = min(cn, i - c0 + 1);
-      if (g.flags & G_TRI_A_UPPER) cl = max(0, i - c0);
-      const T* col = A + i + (int64_t)(c0 + cl) * d.lda;
-      int q = cl;
-      for (; q + 3 < ch; q += 4) {
-        s0 = fma(col[0], xs[q], s0);
-        s1 = fma(col[d.lda], xs[q + 1], s1);
-        s2 = fma(col[2 * (int64_t)d.lda], xs[q + 2], s2);
-        s3 = fma(col[3 * (int64_t)d.lda], xs[q + 3], s3);
-        col += 4 * (int64_t)d.lda;
-      }
-      for (; q < ch; ++q) {
-        s0 = fma(col[0], xs[q], s0);
-        col += d.lda;
+  Acc s;
+  for (int c0 = cbeg + warp * 32; c0 < cend; c0 += 32 * kGemvWarps) {
+    const int cn = min(32, cend - c0);
+    const T xr = lane < cn ? x[c0 + lane] : T(0);
+    const T* __restrict__ col = A + (int64_t)c0 * d.lda;
+    // the chunk touches the diagonal: mask the other triangle per element
+    const bool diag = (lower && c0 + 31 > i0) || (upper && c0 < i0 + 31);
+    if (cn == 32 && !diag) {
+      T a[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) a[j] = col[(int64_t)j * d.lda];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) s.add(a[j], __shfl_sync(0xffffffffu, xr, j));
+    } else {
+      for (int j = 0; j < cn; ++j) {
+        const int c = c0 + j;
+        T a = col[(int64_t)j * d.lda];
+        if ((lower && c > i) || (upper && c < i)) a = T(0);
+        s.add(a, __shfl_sync(0xffffffffu, xr, j));
       }
     }
   }
-  if (i < d.m) {
-    T v = g.alpha * ((s0 + s1) + (s2 + s3));
+  red[warp][lane] = s;
+  __syncthreads();
+  if (warp == 0 && row_ok) {
+    Acc t = red[0][lane];
+#pragma unroll
+    for (int w = 1; w < kGemvWarps; ++w) t.merge(red[w][lane]);
+    T v = g.alpha * (T)t.value();
     T* y = g.Y + d.y;
     if (g.beta != T(0)) v = fma(g.beta, y[i], v);
     y[i] = v;
@@ -576,45 +526,59 @@ __global__ void __launch_bounds__(kGemvRows) k_gemv_n(GemvArgs<T> g) {
 
 template <typename T>
 __global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t(GemvArgs<T> g) {
+  using Acc = typename GemvAcc<T>::type;
+  __shared__ T xs[kGemvXChunk];
   const int di = gemv_find(g, blockIdx.x);
   const GemvDesc d = g.desc[di];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int j = (blockIdx.x - g.prefix[di]) * kGemvCols + warp;   // output index = column of A
-  if (j >= d.n) return;
-  const T* __restrict__ col = g.A + d.a + (int64_t)j * d.lda;
-  const T* __restrict__ x = g.X + d.x;
+  const int j0 = (blockIdx.x - g.prefix[di]) * kGemvCols;
+  const int j = j0 + warp;   // output index = column of A
+  const bool lower = g.flags & G_TRI_A_LOWER, upper = g.flags & G_TRI_A_UPPER;
+  // rows of column j: op(A) = A^T upper <=> rows i >= j; lower <=> rows i <= j
   int ib = 0, ie = d.m;
-  // op(A) = A^T; op(A) upper <=> A lower: only rows i >= j of column j
-  if (g.flags & G_TRI_A_UPPER) ib = min(j, d.m);
-  if (g.flags & G_TRI_A_LOWER) ie = min(d.m, j + 1);
-  T s0 = 0, s1 = 0;
-  int i = ib + lane;
-  for (; i + 32 < ie; i += 64) {
-    s0 = fma(col[i], x[i], s0);
-    s1 = fma(col[i + 32], x[i + 32], s1);
-  }
-  for (; i < ie; i += 32) s0 = fma(col[i], x[i], s0);
-  T s = s0 + s1;
+  if (upper) ib = min(j, d.m);
+  if (lower) ie = min(d.m, j + 1);
+  // rows any column of this CTA reads
+  int cb = 0, ce = d.m;
+  if (upper) cb = min(j0, d.m);
+  if (lower) ce = min(d.m, j0 + kGemvCols);
+  const T* __restrict__ col = g.A + d.a + (int64_t)min(j, d.n - 1) * d.lda;
+  const T* __restrict__ x = g.X + d.x;
+  Acc s;
+  for (int r0 = cb; r0 < ce; r0 += kGemvXChunk) {
+    const int rn = min(kGemvXChunk, ce - r0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < rn; q += blockDim.x) xs[q] = x[r0 + q];
+    __syncthreads();
+    if (j < d.n) {
+      const int lo = max(ib, r0), hi = min(ie, r0 + rn);
+      int r = lo + lane;
+      for (; r + 7 * 32 < hi; r += 8 * 32) {
+        T a[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int u = 0; u < 8; ++u) a[u] = col[r + u * 32];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s.add(a[u], xs[r + u * 32 - r0]);
+      }
+      for (; r < hi; r += 32) s.add(col[r], xs[r - r0]);
+    }
+  }
+  if (j >= d.n) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s.shfl_merge(o);
   if (lane == 0) {
-    T v = g.alpha * s;
+    T v = g.alpha * (T)s.value();
     T* y = g.Y + d.y;
     if (g.beta != T(0)) v = fma(g.beta, y[j], v);
     y[j] = v;
   }
 }
 
-// FP32 products use the compensated kernels, FP64 the plain ones.
+// FP32 products use compensated accumulation, FP64 plain FMA chains.
 template <typename T>
 static void launch_gemv(cudaStream_t st, const GemvArgs<T>& g, unsigned total, bool trans) {
-  if constexpr (std::is_same<T, float>::value) {
-    if (trans) k_gemv_t_df<<<total, 32 * kGemvCols, 0, st>>>(g);
-    else k_gemv_n_df<<<total, kGemvRows, 0, st>>>(g);
-  } else {
-    if (trans) k_gemv_t<T><<<total, 32 * kGemvCols, 0, st>>>(g);
-    else k_gemv_n<T><<<total, kGemvRows, 0, st>>>(g);
-  }
+  if (trans) k_gemv_t<T><<<total, 32 * kGemvCols, 0, st>>>(g);
+  else k_gemv_n<T><<<total, 32 * kGemvWarps, 0, st>>>(g);
 }
 
 template <typename T>
