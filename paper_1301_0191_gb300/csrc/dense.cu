@@ -299,6 +299,10 @@ template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK
 template <typename T> struct GemmSkinny;
 template <> struct GemmSkinny<double> { static constexpr int BM = 64, BN = 16, BK = 16, TM = 4, TN = 2; };
 template <> struct GemmSkinny<float> { static constexpr int BM = 128, BN = 16, BK = 16, TM = 8, TN = 2; };
+// ... and a medium one for 17..32 columns (the Rayleigh-Ritz updates)
+template <typename T> struct GemmMedium;
+template <> struct GemmMedium<double> { static constexpr int BM = 64, BN = 32, BK = 16, TM = 4, TN = 2; };
+template <> struct GemmMedium<float> { static constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2; };
 
 template <typename T, typename TA, typename TL>
 static void gemm_run(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags, T alpha, T beta,
@@ -351,6 +355,8 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   for (const auto& x : d) nmax = std::max(nmax, x.n);
   if (nmax <= 16 && !(flags & G_OUT_LOWER))
     gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C);
+  else if (nmax <= 32 && !(flags & G_OUT_LOWER))
+    gemm_run<T, TA, GemmMedium<T>>(st, ring, d, flags, alpha, beta, A, B, C);
   else
     gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C);
 }

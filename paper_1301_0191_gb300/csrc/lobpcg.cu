@@ -50,19 +50,25 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in shared
-// memory (column-major, leading dimension ld).  Rotations of one round act
-// on disjoint index pairs (round-robin ordering) and are applied together.
+// memory (column-major, leading dimension ld >= n + (n & 1)).  Each round
+// rotates the disjoint index pairs of a round-robin ordering at once, and the
+// two-sided update is applied block-wise: B <- R_k^T B R_l on the 2 x 2 block
+// of index pairs (k, l), k <= l, mirrored to (l, k), with V <- V R in the
+// same pass (one barrier per round; only the upper blocks are computed).  For
+// odd n the extra index n is a zero row and column that is never rotated.
 // On exit A holds the eigenvalues on its diagonal, V the eigenvectors.
 __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, double* cs, double* sn, int* P,
                            int* Q) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  for (int idx = tid; idx < n * n; idx += nt) {
-    int r = idx % n, c = idx / n;
+  const int ne = n + (n & 1), half = ne / 2;
+  for (int idx = tid; idx < ne * ne; idx += nt) {
+    int r = idx % ne, c = idx / ne;
     V[r + c * ld] = (r == c) ? 1.0 : 0.0;
+    if (r == n || c == n) A[r + c * ld] = 0.0;
   }
   __syncthreads();
   if (n <= 1) return;
-  const int ne = n + (n & 1), half = ne / 2;
+  const int nblk = half * (half + 1) / 2;
   for (int sweep = 0; sweep < 40; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = tid; idx < n * n; idx += nt) {
@@ -92,35 +98,53 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, dou
             s = t * c;
           }
         }
-        P[k] = q < n ? p : -1;
+        P[k] = p;
         Q[k] = q;
         cs[k] = c;
         sn[k] = s;
       }
       __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {
-        int k = idx / n, j = idx % n;
-        int p = P[k];
-        if (p < 0 || sn[k] == 0.0) continue;
-        int q = Q[k];
-        double c = cs[k], s = sn[k];
-        double apj = A[p + j * ld], aqj = A[q + j * ld];
-        A[p + j * ld] = c * apj - s * aqj;
-        A[q + j * ld] = s * apj + c * aqj;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {
-        int k = idx / n, i = idx % n;
-        int p = P[k];
-        if (p < 0 || sn[k] == 0.0) continue;
-        int q = Q[k];
-        double c = cs[k], s = sn[k];
-        double aip = A[i + p * ld], aiq = A[i + q * ld];
-        A[i + p * ld] = c * aip - s * aiq;
-        A[i + q * ld] = s * aip + c * aiq;
-        double vip = V[i + p * ld], viq = V[i + q * ld];
-        V[i + p * ld] = c * vip - s * viq;
-        V[i + q * ld] = s * vip + c * viq;
+      for (int idx = tid; idx < nblk + n * half; idx += nt) {
+        if (idx < nblk) {
+          // block (k, l), k <= l, from the triangular index
+          int l = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
+          while (l * (l + 1) / 2 > idx) --l;
+          while ((l + 1) * (l + 2) / 2 <= idx) ++l;
+          const int k = idx - l * (l + 1) / 2;
+          const double sk = sn[k], sl = sn[l];
+          if (sk == 0.0 && sl == 0.0) continue;
+          const double ck = cs[k], cl = cs[l];
+          const int pk = P[k], qk = Q[k], pl = P[l], ql = Q[l];
+          const double b00 = A[pk + pl * ld], b01 = A[pk + ql * ld], b10 = A[qk + pl * ld], b11 = A[qk + ql * ld];
+          const double t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+          const double t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+          const double n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+          const double n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+          if (k == l) {
+            A[pk + pk * ld] = n00;
+            A[qk + qk * ld] = n11;
+            A[pk + qk * ld] = n01;
+            A[qk + pk * ld] = n01;
+          } else {
+            A[pk + pl * ld] = n00;
+            A[pk + ql * ld] = n01;
+            A[qk + pl * ld] = n10;
+            A[qk + ql * ld] = n11;
+            A[pl + pk * ld] = n00;
+            A[ql + pk * ld] = n01;
+            A[pl + qk * ld] = n10;
+            A[ql + qk * ld] = n11;
+          }
+        } else {
+          const int v = idx - nblk, l = v / n, i = v % n;
+          const double sl = sn[l];
+          if (sl == 0.0) continue;
+          const double cl = cs[l];
+          const int pl = P[l], ql = Q[l];
+          const double vp = V[i + pl * ld], vq = V[i + ql * ld];
+          V[i + pl * ld] = cl * vp - sl * vq;
+          V[i + ql * ld] = sl * vp + cl * vq;
+        }
       }
       __syncthreads();
     }
@@ -320,11 +344,12 @@ __global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const 
   extern __shared__ double sh[];
   const int p = blockIdx.x;
   const int n = (int)QP(p, Q_NCP), ncs = (int)QP(p, Q_NCS), nct = (int)QP(p, Q_NCT);
+  const int ld = n + (n & 1);
   double* A = sh;
-  double* V = A + n * n;
+  double* V = A + ld * ld;
   __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
   __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1];
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x) A[i] = 0.0;
+  for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) A[i] = 0.0;
   __syncthreads();
   if (threadIdx.x == 0) {
     const double* as = Ac + acs[p];
@@ -332,22 +357,22 @@ __global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const 
     const int32_t* ms = cms + QP(p, Q_CMS);
     const int32_t* mt = cmt + QP(p, Q_CMT);
     for (int b = 0; b < ncs; ++b)
-      for (int a = 0; a < ncs; ++a) A[ms[a] + ms[b] * n] += as[a + b * ncs];
+      for (int a = 0; a < ncs; ++a) A[ms[a] + ms[b] * ld] += as[a + b * ncs];
     for (int b = 0; b < nct; ++b)
-      for (int a = 0; a < nct; ++a) A[mt[a] + mt[b] * n] += at[a + b * nct];
+      for (int a = 0; a < nct; ++a) A[mt[a] + mt[b] * ld] += at[a + b * nct];
   }
   __syncthreads();
-  jacobi_eig(A, V, n, n, red, cs_, sn_, P_, Q_);
+  jacobi_eig(A, V, n, ld, red, cs_, sn_, P_, Q_);
   double mx = 0.0;
-  for (int i = 0; i < n; ++i) mx = fmax(mx, A[i + i * n]);
+  for (int i = 0; i < n; ++i) mx = fmax(mx, A[i + i * ld]);
   const double tol = 1e-12 * mx;
   T* out = pinv + QP(p, Q_OPI);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     int r = idx % n, c = idx / n;
     double s = 0.0;
     for (int k = 0; k < n; ++k) {
-      double l = A[k + k * n];
-      if (l > tol) s += V[r + k * n] * V[c + k * n] / l;
+      double l = A[k + k * ld];
+      if (l > tol) s += V[r + k * ld] * V[c + k * ld] / l;
     }
     out[idx] = (T)s;
   }
@@ -431,12 +456,13 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   extern __shared__ double sh[];
   const int p = blockIdx.x;
   const int m3 = 3 * m;
+  const int ld = w + (w & 1);   // padded for the Jacobi rounds
   double* GA = sh;
-  double* GB = GA + w * w;
-  double* V = GB + w * w;
-  double* Mr = V + w * w;
-  double* Yr = Mr + w * w;
-  double* dsc = Yr + w * w;   // w
+  double* GB = GA + ld * ld;
+  double* V = GB + ld * ld;
+  double* Mr = V + ld * ld;
+  double* Yr = Mr + ld * ld;
+  double* dsc = Yr + ld * ld;   // w
   __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
   __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1], ord[kJacobiMax], ord2[kJacobiMax];
   __shared__ int rank_sh;
@@ -453,31 +479,31 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   const double* gb = ga + m3 * m3;
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     int r = idx % w, c = idx / w;
-    GA[idx] = 0.5 * (ga[r + c * m3] + ga[c + r * m3]);
-    GB[idx] = 0.5 * (gb[r + c * m3] + gb[c + r * m3]);
+    GA[r + c * ld] = 0.5 * (ga[r + c * m3] + ga[c + r * m3]);
+    GB[r + c * ld] = 0.5 * (gb[r + c * m3] + gb[c + r * m3]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double dmax = 0.0;
-    for (int i = 0; i < w; ++i) dmax = fmax(dmax, GB[i + i * w]);
+    for (int i = 0; i < w; ++i) dmax = fmax(dmax, GB[i + i * ld]);
     for (int i = 0; i < w; ++i) {
-      double d = GB[i + i * w];
+      double d = GB[i + i * ld];
       dsc[i] = (d > 1e-14 * dmax && d > 0.0) ? 1.0 / sqrt(d) : 0.0;
     }
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     int r = idx % w, c = idx / w;
-    GA[idx] *= dsc[r] * dsc[c];
-    GB[idx] *= dsc[r] * dsc[c];
+    GA[r + c * ld] *= dsc[r] * dsc[c];
+    GB[r + c * ld] *= dsc[r] * dsc[c];
   }
   __syncthreads();
-  jacobi_eig(GB, V, w, w, red, cs_, sn_, P_, Q_);
-  sort_desc(GB, w, w, ord);
+  jacobi_eig(GB, V, w, ld, red, cs_, sn_, P_, Q_);
+  sort_desc(GB, w, ld, ord);
   if (threadIdx.x == 0) {
-    double smax = GB[ord[0] + ord[0] * w];
+    double smax = GB[ord[0] + ord[0] * ld];
     int r = 0;
-    while (r < w && GB[ord[r] + ord[r] * w] > drop * smax && smax > 0.0) ++r;
+    while (r < w && GB[ord[r] + ord[r] * ld] > drop * smax && smax > 0.0) ++r;
     rank_sh = r;
   }
   __syncthreads();
@@ -486,35 +512,35 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   for (int idx = threadIdx.x; idx < w * r; idx += blockDim.x) {
     int i = idx % w, k = idx / w;
     int c = ord[k];
-    Yr[i + k * w] = V[i + c * w] / sqrt(GB[c + c * w]);
+    Yr[i + k * ld] = V[i + c * ld] / sqrt(GB[c + c * ld]);
   }
   __syncthreads();
   // V := GA Tm (w x r), then Mr := Tm^T V (r x r)
   for (int idx = threadIdx.x; idx < w * r; idx += blockDim.x) {
     int i = idx % w, k = idx / w;
     double s = 0.0;
-    for (int j = 0; j < w; ++j) s += GA[i + j * w] * Yr[j + k * w];
-    V[i + k * w] = s;
+    for (int j = 0; j < w; ++j) s += GA[i + j * ld] * Yr[j + k * ld];
+    V[i + k * ld] = s;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
     int a = idx % r, b = idx / r;
     double s = 0.0;
-    for (int j = 0; j < w; ++j) s += Yr[j + a * w] * V[j + b * w];
-    Mr[a + b * r] = s;
+    for (int j = 0; j < w; ++j) s += Yr[j + a * ld] * V[j + b * ld];
+    Mr[a + b * ld] = s;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < r * r; idx += blockDim.x) {
     int a = idx % r, b = idx / r;
     if (a > b) {
-      double s = 0.5 * (Mr[a + b * r] + Mr[b + a * r]);
-      Mr[a + b * r] = s;
-      Mr[b + a * r] = s;
+      double s = 0.5 * (Mr[a + b * ld] + Mr[b + a * ld]);
+      Mr[a + b * ld] = s;
+      Mr[b + a * ld] = s;
     }
   }
   __syncthreads();
-  jacobi_eig(Mr, GB, r, r, red, cs_, sn_, P_, Q_);   // eigenvectors into GB (r x r, ld r)
-  sort_desc(Mr, r, r, ord2);
+  jacobi_eig(Mr, GB, r, ld, red, cs_, sn_, P_, Q_);   // eigenvectors into GB (r x r, ld)
+  sort_desc(Mr, r, ld, ord2);
   const int mm = min(m, r);
   // Cx(:, k) = D Tm y_k ; Cp = Cx with the X rows zeroed
   for (int idx = threadIdx.x; idx < m3 * m; idx += blockDim.x) {
@@ -522,7 +548,7 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
     double s = 0.0;
     if (i < w && k < mm) {
       int c = ord2[k];
-      for (int j = 0; j < r; ++j) s += Yr[i + j * w] * GB[j + c * r];
+      for (int j = 0; j < r; ++j) s += Yr[i + j * ld] * GB[j + c * ld];
       s *= dsc[i];
     }
     C[i + (int64_t)k * m3] = (T)s;
@@ -530,7 +556,7 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   }
   if (threadIdx.x < m) {
     int k = threadIdx.x;
-    L[k] = k < mm ? Mr[ord2[k] + ord2[k] * r] : 0.0;
+    L[k] = k < mm ? Mr[ord2[k] + ord2[k] * ld] : 0.0;
   }
 }
 
@@ -562,7 +588,9 @@ __global__ void k_lob_resid(T* Qb, double* rn, double* bn, const double* lam, co
   }
 }
 
-// copy the updated blocks back: Tp = [Xn Pn | AXn APn | BXn BPn] -> panel
+// copy the updated blocks back: Tp = [Xn' Pn | AXn' APn | BXn' BPn] -> panel,
+// where the X-type blocks hold only the X-row part (X Cx_X) and receive the
+// P-type block here: Xn = X Cx_X + Pn (and likewise for AX, BX)
 template <typename T>
 __global__ void k_lob_copyback(T* Qb, const T* Tp, const int64_t* qp, int m, const int* act) {
   const int p = blockIdx.y;
@@ -575,7 +603,9 @@ __global__ void k_lob_copyback(T* Qb, const T* Tp, const int64_t* qp, int m, con
   // within < m: X-type block (slot 0 of the group), else P-type (slot 2)
   const int slot = grp * 3 + (within < m ? 0 : 2);
   const int c = within % m;
-  Qb[QP(p, Q_OQ) + (int64_t)(slot * m + c) * N + row] = Tp[QP(p, Q_OT) + idx];
+  const T* t = Tp + QP(p, Q_OT) + idx;
+  const T v = within < m ? t[0] + t[(int64_t)m * N] : t[0];
+  Qb[QP(p, Q_OQ) + (int64_t)(slot * m + c) * N + row] = v;
 }
 
 // adaptive rows: columns 0..k-1 of A X restricted to the face dofs (s copy),
@@ -811,7 +841,8 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   }
   // pseudo-inverse of the pair coarse matrices (initial constraints)
   {
-    const size_t smem = (size_t)2 * max_ncp * max_ncp * sizeof(double);
+    const int nl = max_ncp + (max_ncp & 1);
+    const size_t smem = (size_t)2 * nl * nl * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_pair_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
     k_pair_pinv<T><<<np, 256, smem, st>>>(dptr<T>(Pinv), QPd, dptr<double>(L.Ac), dptr<int64_t>(dacs),
                                           dptr<int64_t>(dact), dptr<int32_t>(dcms), dptr<int32_t>(dcmt), dptr<int>(status));
@@ -958,24 +989,30 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   auto rayleigh_ritz = [&](int w) {
     k_lob_gram<V><<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), Q, QPd, m, w, dptr<int>(act_d));
     AMB_LAUNCHED();
-    const size_t smem = (size_t)(5 * w * w + w) * sizeof(double);
+    const int wl = w + (w & 1);
+    const size_t smem = (size_t)(5 * wl * wl + wl) * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_lob_rr<V><<<np, 256, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
                                        svqb_drop);
     AMB_LAUNCHED();
-    // [Xn Pn] = U Cc, [AXn APn] = AU Cc, [BXn BPn] = BU Cc
-    std::vector<GemmDesc> d;
-    for (int g = 0; g < 3; ++g) {
-      d.clear();
-      for (int p = 0; p < np; ++p) {
-        const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
-        if (!active[p]) continue;
-        const int64_t N = q[Q_N];
-        d.push_back(GemmDesc{(int)N, 2 * m, w, (int)N, m3, (int)N, q[Q_OQ] + (int64_t)3 * g * m * N, q[Q_OCC],
-                             q[Q_OT] + (int64_t)2 * g * m * N});
+    // [Xn Pn] = U [Cx | Cp] with Cp = Cx with the X rows zeroed, so
+    // Pn = U(:, m:w) Cx(m:w, :) and Xn = U(:, 0:m) Cx(0:m, :) + Pn: two
+    // products of N x m x (w-m) and N x m x m instead of N x 2m x w (the sum
+    // is formed in the copy-back).  Same for AU and BU.
+    std::vector<GemmDesc> dp, dx;
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
+      const int64_t N = q[Q_N];
+      for (int g = 0; g < 3; ++g) {
+        const int64_t u = q[Q_OQ] + (int64_t)3 * g * m * N, t = q[Q_OT] + (int64_t)2 * g * m * N;
+        dp.push_back(GemmDesc{(int)N, m, w - m, (int)N, m3, (int)N, u + (int64_t)m * N, q[Q_OCC] + m,
+                              t + (int64_t)m * N});
+        dx.push_back(GemmDesc{(int)N, m, m, (int)N, m3, (int)N, u, q[Q_OCC], t});
       }
-      gemm_batched<V>(st, ring, d, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     }
+    gemm_batched<V>(st, ring, dp, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
+    gemm_batched<V>(st, ring, dx, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     k_lob_copyback<V><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<V>(Tp), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
   };
