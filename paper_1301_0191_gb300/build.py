@@ -20,7 +20,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libamb.so")
 
-SOURCES = ["dense.cu", "kernels.cu", "fem.cu", "engine.cu", "lobpcg.cu", "api.cu", "noalloc.cu", "topology.cpp"]
+SOURCES = ["dense.cu", "tc_gemm.cu", "kernels.cu", "fem.cu", "engine.cu", "lobpcg.cu", "api.cu", "noalloc.cu", "topology.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

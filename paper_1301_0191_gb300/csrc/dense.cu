@@ -10,6 +10,7 @@
 #include <type_traits>
 
 #include "common.h"
+#include "tc_gemm.h"
 
 namespace amb {
 
@@ -737,6 +738,7 @@ void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDes
   // matrix is updated once per outer block with K = kOuter, which cuts the
   // passes over the trailing matrix (and its memory traffic) by kOuter/kNB.
   constexpr int kOuter = 4 * kNB;
+  static_assert(kOuter <= kTcKMax, "outer block wider than the tensor-core slab");
   if (d.empty()) return;
   int maxouter = 0;
   for (const auto& x : d) maxouter = std::max(maxouter, (x.c1 - x.c0 + kOuter - 1) / kOuter);
@@ -799,7 +801,16 @@ void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDes
                                x.off + J1 + (int64_t)J0 * x.ld, x.off + J1 + (int64_t)J1 * x.ld});
       if (flops) *flops += (double)rem * (rem + 1) * (J1 - J0);
     }
-    if (!trail.empty()) gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
+    if (trail.empty()) continue;
+    if constexpr (std::is_same<T, float>::value) {
+      // FP32 form: tensor cores (3xTF32, FP32 accuracy)
+      std::vector<TcSyrk> tc;
+      tc.reserve(trail.size());
+      for (const auto& g : trail) tc.push_back(TcSyrk{g.a, g.c, g.lda, g.m, g.k, 0});
+      tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
+    } else {
+      gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
+    }
   }
 }
 

@@ -33,6 +33,9 @@ enum PairField {
 #define QP(p, f) qp[(int64_t)(p) * Q_NPAIRF + (f)]
 
 constexpr int kJacobiMax = 112;
+// Threads of the Jacobi kernels: the rotation rounds are FP64-bound on one
+// SM, and 32 warps keep its FP64 pipes busier than 8 (latency hiding).
+constexpr int kJacobiThreads = 1024;
 
 // ---------------------------------------------------------------- block helpers
 
@@ -339,7 +342,7 @@ __global__ void k_lob_cscatter(T* C, const int64_t* qp, int m, const int32_t* cm
 // pseudo-inverse of the pair coarse matrix Psi^T S^{st} Psi (Sec. 5: dense
 // eigen-decomposition, eigenvalues below a tolerance dropped)
 template <typename T>
-__global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const int64_t* acs, const int64_t* act,
+__global__ void __launch_bounds__(kJacobiThreads) k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const int64_t* acs, const int64_t* act,
                             const int32_t* cms, const int32_t* cmt, int* status) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
@@ -347,7 +350,7 @@ __global__ void k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const 
   const int ld = n + (n & 1);
   double* A = sh;
   double* V = A + ld * ld;
-  __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
+  __shared__ double red[kJacobiThreads], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
   __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1];
   for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) A[i] = 0.0;
   __syncthreads();
@@ -451,7 +454,7 @@ __global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int
 // reduced standard eigenproblem; coefficients Cc = [Cx | Cp] (3m x 2m, T)
 // and the m largest Ritz values.  Frozen pairs keep X (Cx = I, Cp = 0).
 template <typename T>
-__global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w,
+__global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w,
                          double drop) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
@@ -463,7 +466,7 @@ __global__ void k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp,
   double* Mr = V + ld * ld;
   double* Yr = Mr + ld * ld;
   double* dsc = Yr + ld * ld;   // w
-  __shared__ double red[256], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
+  __shared__ double red[kJacobiThreads], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
   __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1], ord[kJacobiMax], ord2[kJacobiMax];
   __shared__ int rank_sh;
   T* C = Cc + QP(p, Q_OCC);
@@ -844,7 +847,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     const int nl = max_ncp + (max_ncp & 1);
     const size_t smem = (size_t)2 * nl * nl * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_pair_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
-    k_pair_pinv<T><<<np, 256, smem, st>>>(dptr<T>(Pinv), QPd, dptr<double>(L.Ac), dptr<int64_t>(dacs),
+    k_pair_pinv<T><<<np, kJacobiThreads, smem, st>>>(dptr<T>(Pinv), QPd, dptr<double>(L.Ac), dptr<int64_t>(dacs),
                                           dptr<int64_t>(dact), dptr<int32_t>(dcms), dptr<int32_t>(dcmt), dptr<int>(status));
     AMB_LAUNCHED();
   }
@@ -992,7 +995,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     const int wl = w + (w & 1);
     const size_t smem = (size_t)(5 * wl * wl + wl) * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lob_rr<V><<<np, 256, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
+    k_lob_rr<V><<<np, kJacobiThreads, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
                                        svqb_drop);
     AMB_LAUNCHED();
     // [Xn Pn] = U [Cx | Cp] with Cp = Cx with the X rows zeroed, so
@@ -1031,7 +1034,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const double tau = cfg.tau;
   std::vector<double> resid(np, 0.0), best(np, 1e300);
   std::vector<int> since(np, 0);
-  constexpr int kStall = 20;
+  // stagnation: far from tol, kStall iterations without halving the worst
+  // used residual; within kFloor x tol (the residual floor of the operator
+  // products, reached by some pairs of the FP32 form), kFloorStall
+  constexpr int kStall = 20, kFloorStall = 3;
+  constexpr double kFloor = 10.0;
   auto check = [&]() {
     k_lob_resid<V><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
@@ -1059,15 +1066,16 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       }
       resid[p] = worst;
       conv[p] = ok ? 1 : 0;
-      // stagnation: a pair whose worst used residual has not halved within
-      // kStall iterations stops iterating (reported as not converged)
+      // a stagnating pair stops iterating (reported as not converged, with
+      // its residual)
       if (worst < 0.5 * best[p]) {
         best[p] = worst;
         since[p] = 0;
       } else {
         ++since[p];
       }
-      active[p] = (ok || since[p] >= kStall) ? 0 : 1;
+      const bool stalled = since[p] >= kStall || (worst <= kFloor * tol && since[p] >= kFloorStall);
+      active[p] = (ok || stalled) ? 0 : 1;
       nact += active[p];
     }
     return nact;

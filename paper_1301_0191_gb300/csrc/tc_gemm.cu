@@ -1,0 +1,421 @@
+// Trailing update of the blocked Cholesky (Sec. 2: A_II = L L^T and, through
+// the same elimination, S = K_GG - X^T X) on the 5th-generation tensor cores:
+//
+//   C(lower) = beta C + alpha P P^T,   P = rem x K, C = rem x rem,
+//
+// in FP32 accuracy from three TF32 products (P = P_h + P_l, both TF32-exact:
+// P P^T ~ P_h P_h^T + P_h P_l^T + P_l P_h^T, the P_l P_l^T term is below FP32
+// rounding).  A split pass writes P_h and P_l row-major (K contiguous, the
+// K-major operand layout of tcgen05.mma kind::tf32) into a workspace slab,
+// each substructure's rows padded to a multiple of 128 and K to a multiple
+// of 32, with zeros.
+//
+// The tile kernel is persistent (one CTA per SM, 128 x 128 output tiles
+// taken round-robin) and warp-specialized: warp 0 loads 128 x 32 operand
+// tiles with TMA (128-byte swizzle) into a 3-stage shared-memory ring, warp 1
+// owns the TMEM accumulators and issues the MMAs (one thread), and warps 2-5
+// drain the accumulators with tcgen05.ld (lane = row), hand TMEM back to the
+// MMA warp and then update C, so the next tile's MMAs overlap the epilogue's
+// C traffic.  Stage hand-offs use mbarriers: TMA completion (expect_tx),
+// MMA completion (tcgen05.commit), TMEM full / TMEM empty.
+//
+// Accuracy: the tensor cores' FP32 accumulation rounds toward zero, so a
+// single accumulator collecting all three products drifts on sums of like
+// sign (the diagonal of P P^T): about 10x the error of an FP32 FMA chain at
+// K = 256.  The K = 8 steps of P_h P_h^T therefore rotate over three TMEM
+// accumulators, the small cross terms go to a fourth, and the epilogue adds
+// the four with round-to-nearest; measured against exact sums this is as
+// accurate as an FP32 FMA chain (rms 2.4e-8 vs 2.8e-8 relative to sum |terms|
+// for random signs, 4.0e-7 vs 2.5e-7 for positive terms, K = 256).  Every wait
+// is bounded: a wait that runs out sets AMB_ETIMEOUT in the status word and
+// raises a CTA-wide abort flag; every role then leaves its loop and TMEM is
+// released.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "common.h"
+#include "tc_gemm.h"
+
+namespace amb {
+
+namespace {
+
+constexpr int kTM = 128, kTN = 128, kTK = 32, kStages = 3;
+constexpr int kTileBytes = kTM * kTK * 4;        // one operand tile (16 KB)
+constexpr int kStageBytes = 4 * kTileBytes;      // A_h, A_l, B_h, B_l
+constexpr int kSmemBytes = kStages * kStageBytes + 1024;
+constexpr int kAccCols = 4 * kTN;                  // three P_h P_h^T accumulators + one for the cross terms
+constexpr long kSpinLimit = 1L << 22;            // polls per wait (~0.5 s with backoff)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTN >> 3) << 17) |
+                            ((uint32_t)(kTM >> 4) << 24);
+
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tacc, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// P (rem x K, column-major, ld) -> slab rows [row0, row0 + rpad), K-contiguous,
+// stride kp; entries outside rem x K are zero.  32 x 32 tiles through shared
+// memory (coalesced on both sides).
+__global__ void k_tc_split(const float* base, const TcSplitDesc* d, int kp, float* sh, float* sl) {
+  __shared__ float t[32][33];
+  const TcSplitDesc x = d[blockIdx.z];
+  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  if (r0 >= x.rpad || k0 >= kp) return;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int q = ty; q < 32; q += 8) {
+    const int r = r0 + tx, k = k0 + q;
+    t[q][tx] = (r < x.rows && k < x.cols) ? base[x.src + r + (int64_t)k * x.ld] : 0.f;
+  }
+  __syncthreads();
+  for (int q = ty; q < 32; q += 8) {
+    const float v = t[tx][q];
+    const float h = tf32_round(v);
+    const int64_t o = (x.row0 + r0 + q) * (int64_t)kp + k0 + tx;
+    sh[o] = h;
+    sl[o] = tf32_round(v - h);
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// shared-memory descriptor of a K-major tile written by TMA with 128-byte
+// swizzle: 8 rows x 128 B swizzle atoms, 1024 B between 8-row groups
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// bounded wait that also gives up when another role has aborted
+__device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (it > 32) __nanosleep(64);
+  }
+  *abort_flag = 1;
+  if (status) atomicCAS(status, 0, AMB_ETIMEOUT);
+  return false;
+}
+
+__device__ __forceinline__ void tile_coords(const TcTileArgs& g, int tile, TcDesc& d, int& ti, int& tj) {
+  int lo = 0, hi = g.ndesc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  d = g.desc[lo];
+  const int t = tile - g.prefix[lo];
+  if (d.lower) {
+    ti = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+    while (ti * (ti + 1) / 2 > t) --ti;
+    while ((ti + 1) * (ti + 2) / 2 <= t) ++ti;
+    tj = t - ti * (ti + 1) / 2;
+  } else {
+    const int tn = (d.n + kTN - 1) / kTN;
+    ti = t / tn;
+    tj = t % tn;
+  }
+}
+
+__global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUtensorMap map_h,
+                                                   const __grid_constant__ CUtensorMap map_l, TcTileArgs g) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull, tempty;
+  __shared__ uint32_t tbase;
+  __shared__ volatile int abort_sh;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(kAccCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[s])), "r"(1) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfull)), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty)), "r"(4) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_h) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l) : "memory");
+    abort_sh = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tacc = tbase;
+  const int ntiles = g.prefix[g.ndesc];
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x) {
+        TcDesc d;
+        int ti, tj;
+        tile_coords(g, tile, d, ti, tj);
+        const int ya = (int)(d.arow + (int64_t)ti * kTM), yb = (int)(d.brow + (int64_t)tj * kTN);
+        const int nk = d.k / kTK;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % kStages;
+          if (!role_wait(smem_u32(&empty[s]), ((it / kStages) & 1) ^ 1, &abort_sh, g.status)) break;
+          const uint32_t sb = smem_u32(smem + s * kStageBytes), fb = smem_u32(&full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageBytes) : "memory");
+          tma_load_2d(sb, &map_h, kt * kTK, ya, fb);
+          tma_load_2d(sb + kTileBytes, &map_l, kt * kTK, ya, fb);
+          tma_load_2d(sb + 2 * kTileBytes, &map_h, kt * kTK, yb, fb);
+          tma_load_2d(sb + 3 * kTileBytes, &map_l, kt * kTK, yb, fb);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, tl = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x, ++tl) {
+        TcDesc d;
+        int ti, tj;
+        tile_coords(g, tile, d, ti, tj);
+        const int nk = d.k / kTK;
+        if (!role_wait(smem_u32(&tempty), (tl & 1) ^ 1, &abort_sh, g.status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % kStages;
+          if (!role_wait(smem_u32(&full[s]), (it / kStages) & 1, &abort_sh, g.status)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sb = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+          for (int kk = 0; kk < kTK / 8; ++kk) {
+            const uint32_t ko = kk * 32;   // K = 8 per MMA: 32 bytes along the swizzled row
+            const uint64_t dah = smem_desc_sw128(sb + ko), dal = smem_desc_sw128(sb + kTileBytes + ko);
+            const uint64_t dbh = smem_desc_sw128(sb + 2 * kTileBytes + ko), dbl = smem_desc_sw128(sb + 3 * kTileBytes + ko);
+            const int step = kt * (kTK / 8) + kk;
+            mma_tf32(tacc + (uint32_t)((step % 3) * kTN), dah, dbh, step >= 3 ? 1u : 0u);
+            mma_tf32(tacc + (uint32_t)(3 * kTN), dah, dbl, step >= 1 ? 1u : 0u);
+            mma_tf32(tacc + (uint32_t)(3 * kTN), dal, dbh, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[s]))
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&tfull))
+                     : "memory");
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2..5)
+    const int quad = warp & 3;   // TMEM lanes 32*quad .. 32*quad + 31
+    uint32_t tl = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x, ++tl) {
+      TcDesc d;
+      int ti, tj;
+      tile_coords(g, tile, d, ti, tj);
+      const int nsteps = (d.k / kTK) * (kTK / 8);
+      if (!role_wait(smem_u32(&tfull), tl & 1, &abort_sh, g.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float acc[kTN];
+#pragma unroll
+      for (int q = 0; q < kTN; ++q) acc[q] = 0.f;
+#pragma unroll
+      for (int cb = 0; cb < kTN / 32; ++cb) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (a < 3 && a >= nsteps) continue;
+          uint32_t r[32];
+          const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTN + cb * 32);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
+              "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+                "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[cb * 32 + q] += __uint_as_float(r[q]);
+        }
+      }
+      // TMEM back to the MMA warp before the C traffic
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty)) : "memory");
+      const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
+      if (i < d.m) {
+        float* row = g.c + d.c + i;
+#pragma unroll
+        for (int cb = 0; cb < kTN / 32; ++cb) {
+          // all loads of the chunk first, then the stores
+          const int j0 = tj * kTN + cb * 32;
+          float cv[32];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int j = j0 + q;
+            const bool w = j < d.n && !(d.lower && j > i);
+            cv[q] = (w && g.beta != 0.f) ? __ldcg(row + (int64_t)j * d.ldc) : 0.f;
+          }
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int j = j0 + q;
+            if (j >= d.n || (d.lower && j > i)) continue;
+            row[(int64_t)j * d.ldc] = fmaf(g.beta, cv[q], g.alpha * acc[cb * 32 + q]);
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(kAccCols) : "memory");
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    AMB_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    AMB_CHECK(p != nullptr && q == cudaDriverEntryPointSuccess, AMB_ECUDA, "cuTensorMapEncodeTiled not available");
+    return (EncodeTiledFn)p;
+  }();
+  return fn;
+}
+
+// 2-D map over a slab (rows x kp FP32, row-major) with 128 x 32 boxes, 128-byte swizzle
+CUtensorMap slab_map(float* base, int64_t rows, int kp) {
+  CUtensorMap m;
+  const cuuint64_t dim[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)kp * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM}, estr[2] = {1, 1};
+  const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dim, stride, box, estr,
+                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  AMB_CHECK(r == CUDA_SUCCESS, AMB_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return m;
+}
+
+// workspace slab for the split operands, grown on demand
+float* tc_slab(size_t floats) {
+  static thread_local DevBuf buf;
+  const size_t need = 2 * floats * sizeof(float);
+  if (buf.bytes < need) {
+    AMB_CUDA(cudaDeviceSynchronize());   // earlier launches may still read the old slab
+    buf.alloc(need);
+  }
+  return dptr<float>(buf);
+}
+
+}  // namespace
+
+int tc_tile_count(const TcDesc& x) {
+  const int tm = (x.m + kTM - 1) / kTM;
+  if (x.m <= 0 || x.n <= 0) return 0;
+  if (x.lower) return tm * (tm + 1) / 2;
+  return tm * ((x.n + kTN - 1) / kTN);
+}
+
+void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, float alpha, float beta,
+                   float* base, int* status) {
+  if (d.empty()) return;
+  static thread_local bool attr = false;
+  if (!attr) {
+    AMB_CUDA(cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    attr = true;
+  }
+  constexpr int kp = kTcKMax;
+  std::vector<TcSplitDesc> sp;
+  std::vector<TcDesc> td;
+  std::vector<int> prefix;
+  int64_t rows = 0;
+  int maxr = 0;
+  int64_t tiles = 0;
+  for (const auto& x : d) {
+    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
+    if (x.rem <= 0 || x.k <= 0) continue;
+    const int rpad = (x.rem + kTM - 1) / kTM * kTM;
+    sp.push_back(TcSplitDesc{x.p, rows, x.ld, x.rem, x.k, rpad});
+    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0};
+    prefix.push_back((int)tiles);
+    tiles += tc_tile_count(t);
+    td.push_back(t);
+    rows += rpad;
+    maxr = std::max(maxr, rpad);
+  }
+  if (td.empty()) return;
+  AMB_CHECK(tiles < (1LL << 31) && sp.size() < 65536, AMB_EINVAL, "tensor-core batch too large");
+  prefix.push_back((int)tiles);
+  float* sh = tc_slab((size_t)rows * kp);
+  float* sl = sh + (size_t)rows * kp;
+  const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(sp.data(), sp.size() * sizeof(TcSplitDesc), st));
+  k_tc_split<<<dim3((unsigned)(maxr / 32), kp / 32, (unsigned)sp.size()), dim3(32, 8), 0, st>>>(base, dsp, kp, sh, sl);
+  AMB_LAUNCHED();
+  std::vector<char> blob(td.size() * sizeof(TcDesc) + prefix.size() * sizeof(int));
+  memcpy(blob.data(), td.data(), td.size() * sizeof(TcDesc));
+  memcpy(blob.data() + td.size() * sizeof(TcDesc), prefix.data(), prefix.size() * sizeof(int));
+  char* dev = static_cast<char*>(ring.push(blob.data(), blob.size(), st));
+  TcTileArgs g;
+  g.desc = reinterpret_cast<const TcDesc*>(dev);
+  g.prefix = reinterpret_cast<const int*>(dev + td.size() * sizeof(TcDesc));
+  g.ndesc = (int)td.size();
+  g.kp = kp;
+  g.alpha = alpha;
+  g.beta = beta;
+  g.ah = sh;
+  g.al = sl;
+  g.bh = sh;
+  g.bl = sl;
+  g.c = base;
+  g.status = status;
+  static thread_local int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    AMB_CUDA(cudaGetDevice(&dev));
+    AMB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const CUtensorMap mh = slab_map(sh, rows, kp), ml = slab_map(sl, rows, kp);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
+  k_tc_syrk<<<grid, 192, kSmemBytes, st>>>(mh, ml, g);
+  AMB_LAUNCHED();
+}
+
+}  // namespace amb
