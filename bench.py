@@ -31,6 +31,9 @@ import amb_inputs as ai  # noqa: E402
 
 METRIC = "adaptive-BDDC setup+solve s to 1e-8 rel. residual; Schur-apply % of roofline"
 WORKLOAD = "elasticity48_4x4x4_lognormal"
+# DRAM bytes per algorithmic flop of the tensor-core trailing update, from the ncu capture summarised in
+# profiles/k_tc_syrk_elasticity48_block2x2x2.md (None when the kernel has changed since)
+TC_TRAFFIC_PER_FLOP = None
 
 
 def _peaks():
@@ -249,17 +252,53 @@ def main():
     rep = c.report()
     peaks, src = _peaks()
     fams = st["families"]
-    fam_factor = fams["factor"]
     fp = "fp32" if prec == B.FP32 else "fp64"
     # SIMT FP32: 152 SMs x 128 lanes x 2 flops x max SM clock; FP64: nominal 1.25 TFLOP/s
     alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if fp == "fp32" else 1.25
-    achieved = li.factor_flops / (fam_factor["ms"] * 1e-3) / 1e12 if fam_factor["ms"] > 0 else None
-    roofline = {"kernel": "batched partial Cholesky (k_chol_diag + k_gemm panel/trailing)", "bound": "alu",
-                "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak if achieved else None, "traffic": None,
-                "peak_source": f"derived: {fp} SIMT lanes x clock ({src} peaks file)"}
+    # TF32 tensor peak: the measured dense BF16 burst times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
+    tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+    # per-substructure sizes of level 1: (n_I, n_Gamma, n_corner, n_c)
+    sz = np.array([c.export(B.X_SUB_SIZES, 1, s, np.int32)[:4] for s in range(li.n_subs)], dtype=np.float64)
+    n_i, n_g, n_d = sz[:, 0], sz[:, 1], sz[:, 1] - sz[:, 2]
+    sizes = [int(v) for v in n_g]
+    # factorization a2-a5: algorithmic flops sum(n_I^3/3 + n_I^2 n_G + n_I n_G^2 + n_D^3/3)
+    fact_flops = float(np.sum(n_i ** 3 / 3 + n_i ** 2 * n_g + n_i * n_g ** 2 + n_d ** 3 / 3))
+    f_ms = fams["factor"]["ms"]
+    factorization = {"algorithmic_flops": fact_flops, "ms": f_ms,
+                     "TFLOP/s": fact_flops / (f_ms * 1e-3) / 1e12 if f_ms > 0 else None,
+                     "tf32_peak": tf32_peak, "frac_of_tf32_peak": fact_flops / (f_ms * 1e-3) / 1e12 / tf32_peak
+                     if f_ms > 0 else None, "trtri_ms": fams["trtri"]["ms"],
+                     "note": "factor family = Cholesky of A_II (whose trailing updates also form S) and of S_DD; "
+                             "the explicit triangular inverses (trtri) are timed apart"}
+    # dominant factorization kernel: the tensor-core trailing update (FP32 form)
+    tc = fams["tc_trailing"]
+    if fp == "fp32" and tc["ms"] > 0:
+        ach = tc["flops"] / (tc["ms"] * 1e-3) / 1e12
+        roofline = {"kernel": "k_tc_syrk (+ k_tc_split): Cholesky trailing update C -= P P^T, 3xTF32 on tcgen05",
+                    "bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
+                    "tensor_pipe_frac": 3.0 * ach / tf32_peak, "traffic": TC_TRAFFIC_PER_FLOP * tc["flops"] / tc["launches"]
+                    if TC_TRAFFIC_PER_FLOP and tc["launches"] else None,
+                    "launches": tc["launches"], "ms": tc["ms"],
+                    "peak_source": f"{src} bf16 dense burst x nominal TF32/BF16 ratio (of {src})",
+                    "units": "flops = 2 per lower-triangle multiply-add; tensor_pipe_frac counts the three TF32 "
+                             "products of each"}
+    else:
+        achieved = fact_flops / (f_ms * 1e-3) / 1e12 if f_ms > 0 else None
+        roofline = {"kernel": "batched partial Cholesky (k_chol_diag + k_gemm panel/trailing, FP64)", "bound": "alu",
+                    "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                    "frac": achieved / alu_peak if achieved else None, "traffic": None,
+                    "peak_source": f"nominal {fp} rate"}
+    # Algorithm-1 preconditioner: bytes per application streamed by the GEMVs (triangles of the explicit
+    # inverses, K_IG twice, Psi twice)
+    esz_f = 4 if fp == "fp32" else 8
+    nc = sz[:, 3]
+    pre_bytes = esz_f * float(np.sum(n_i ** 2 + n_d ** 2 + 2 * n_i * n_g + 2 * n_g * nc))
+    pre = fams["precond"]
+    # one application before the first PCG iteration and one after each non-final one
+    precond = {"bytes_per_apply": pre_bytes, "applies": int(info.iterations), "ms": pre["ms"]}
+    precond["GB/s"] = pre_bytes * precond["applies"] / (pre["ms"] * 1e-3) / 1e9 if pre["ms"] > 0 else None
+    precond["hbm_frac"] = precond["GB/s"] / peaks["hbm_gbs"] if precond["GB/s"] else None
     # Schur apply at widths 1, 30, 180 (headline 2)
-    sizes = [int(c.export(B.X_SUB_SIZES, 1, s, np.int32)[1]) for s in range(li.n_subs)]
     tdt = torch.float32 if prec == B.FP32 else torch.float64
     esz = 4 if prec == B.FP32 else 8
     schur = {}
@@ -314,10 +353,12 @@ def main():
                 "pcg_iterations": last.iterations, "rel_residual": last.rel_residual,
                 "true_rel_residual": last.true_rel_residual, "cond_estimate": last.cond_estimate,
                 "n_adaptive": rep["n_adaptive"], "omega": rep["omega"],
-                "phase_ms": st["phase_ms"], "families": fams,
+                "phase_ms": st["phase_ms"],
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches / args.steps), "clocks": clk, "roofline": roofline,
-                "schur_apply": schur, "fp64_form": fp64_form, "cpu_baseline": cpu}
+                "schur_apply": schur, "factorization": factorization, "precond": precond,
+                "families": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in fams.items()},
+                "fp64_form": fp64_form, "cpu_baseline": cpu}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

@@ -145,7 +145,9 @@ typedef struct {
 #define AMB_FAM_PRECOND  4   /* one Algorithm-1 application */
 #define AMB_FAM_OPERATOR 5   /* matrix-free FP64 A p */
 #define AMB_FAM_COARSE   6   /* coarse basis, coarse matrices and top factorization */
-#define AMB_FAM_N        7
+#define AMB_FAM_TC       7   /* FP32 form: tensor-core trailing updates of the factorization
+                                (part of AMB_FAM_FACTOR; flops = rem (rem + 1) K per update) */
+#define AMB_FAM_N        8
 typedef struct {
   double ms[AMB_FAM_N];         /* summed event time */
   int64_t launches[AMB_FAM_N];  /* kernel launches counted in the family */

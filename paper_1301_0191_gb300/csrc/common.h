@@ -182,9 +182,10 @@ struct CholDesc {
   int32_t zld;
   int32_t id;       // substructure id for error reports
 };
+struct Timers;
 template <typename T>
 void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDesc>& d, T* base,
-                      T* zbase, int* status, double* flops);
+                      T* zbase, int* status, double* flops, Timers* tm = nullptr, bool timing = false);
 
 // Explicit inverse of the lower-triangular factor of order n stored at
 // L (ld) into Z (zld), whose nb x nb diagonal blocks already hold the

@@ -11,6 +11,7 @@
 
 #include "common.h"
 #include "tc_gemm.h"
+#include "timers.h"
 
 namespace amb {
 
@@ -304,6 +305,10 @@ template <> struct GemmSkinny<float> { static constexpr int BM = 128, BN = 16, B
 template <typename T> struct GemmMedium;
 template <> struct GemmMedium<double> { static constexpr int BM = 64, BN = 32, BK = 16, TM = 4, TN = 2; };
 template <> struct GemmMedium<float> { static constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2; };
+// ... and a half-wide one (FP32) for 33..64 columns (the Cholesky strip and
+// panel updates; an in-place panel update needs one CTA to own whole rows,
+// which holds because the tile is at least as wide as the product)
+struct GemmHalfF { static constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4; };
 
 template <typename T, typename TA, typename TL>
 static void gemm_run(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags, T alpha, T beta,
@@ -354,12 +359,22 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
                   T alpha, T beta, const TA* A, const T* B, T* C) {
   int nmax = 0;
   for (const auto& x : d) nmax = std::max(nmax, x.n);
-  if (nmax <= 16 && !(flags & G_OUT_LOWER))
+  const bool narrow_ok = !(flags & G_OUT_LOWER);
+  if (nmax <= 16 && narrow_ok) {
     gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C);
-  else if (nmax <= 32 && !(flags & G_OUT_LOWER))
+    return;
+  }
+  if (nmax <= 32 && narrow_ok) {
     gemm_run<T, TA, GemmMedium<T>>(st, ring, d, flags, alpha, beta, A, B, C);
-  else
-    gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C);
+    return;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (nmax <= 64 && narrow_ok) {
+      gemm_run<T, TA, GemmHalfF>(st, ring, d, flags, alpha, beta, A, B, C);
+      return;
+    }
+  }
+  gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C);
 }
 
 template <typename T>
@@ -730,7 +745,7 @@ static T* diag_scratch(size_t nblocks) {
 
 template <typename T>
 void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDesc>& d, T* base,
-                      T* zbase, int* status, double* flops) {
+                      T* zbase, int* status, double* flops, Timers* tm, bool timing) {
   // Two-level blocking: inner panels of kNB columns (diagonal factor +
   // inverse, panel solve) inside outer blocks of kOuter columns.  Inside an
   // outer block the next panel's columns are brought up to date from the
@@ -806,16 +821,28 @@ void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDes
       // FP32 form: tensor cores (3xTF32, FP32 accuracy)
       std::vector<TcSyrk> tc;
       tc.reserve(trail.size());
-      for (const auto& g : trail) tc.push_back(TcSyrk{g.a, g.c, g.lda, g.m, g.k, 0});
-      tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
+      double tfl = 0.0;
+      for (const auto& g : trail) {
+        tc.push_back(TcSyrk{g.a, g.c, g.lda, g.m, g.k, 0});
+        tfl += (double)g.m * (g.m + 1) * g.k;
+      }
+      if (tm) {
+        FamTimer ft(st, tm, AMB_FAM_TC, timing);
+        tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
+        tm->fam_flops[AMB_FAM_TC] += tfl;
+      } else {
+        tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
+      }
     } else {
       gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
     }
   }
 }
 
-template void partial_cholesky<float>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, float*, float*, int*, double*);
-template void partial_cholesky<double>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, double*, double*, int*, double*);
+template void partial_cholesky<float>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, float*, float*, int*, double*,
+                                       Timers*, bool);
+template void partial_cholesky<double>(cudaStream_t, DescRing&, const std::vector<CholDesc>&, double*, double*, int*, double*,
+                                        Timers*, bool);
 
 // ------------------------------------------------------------------ TRTRI
 // [L11 0; L21 L22]^{-1} = [Z11 0; -Z22 L21 Z11, Z22], merged bottom-up from

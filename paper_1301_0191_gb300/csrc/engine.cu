@@ -200,14 +200,14 @@ void Engine<T>::factor_level(LevelData<T>& L) {
     std::vector<CholDesc> d1;
     for (int s = 0; s < ns; ++s)
       d1.push_back(CholDesc{L.pM.off[s], L.nn[s], L.nn[s], 0, L.ni[s], L.pLI.off[s], std::max(L.ni[s], 1), s});
-    partial_cholesky<T>(st, ring, d1, dptr<T>(L.M), dptr<T>(L.LinvI), dptr<int>(status), &fl);
+    partial_cholesky<T>(st, ring, d1, dptr<T>(L.M), dptr<T>(L.LinvI), dptr<int>(status), &fl, &tm, timing());
     check_status("interior factorization A_II = L L^T", AMB_ENOTSPD);
     copy_schur<T>(st, dptr<T>(L.S), dptr<T>(L.M), par, ns, imax(L.ng));
     std::vector<CholDesc> d2;
     for (int s = 0; s < ns; ++s)
       d2.push_back(CholDesc{L.pM.off[s], L.nn[s], L.nn[s], L.ni[s], L.ni[s] + L.nd[s], L.pLD.off[s],
                             std::max(L.nd[s], 1), s});
-    partial_cholesky<T>(st, ring, d2, dptr<T>(L.M), dptr<T>(L.LinvD), dptr<int>(status), &fl);
+    partial_cholesky<T>(st, ring, d2, dptr<T>(L.M), dptr<T>(L.LinvD), dptr<int>(status), &fl, &tm, timing());
     check_status("corner-constrained Neumann factorization S_DD = L_D L_D^T (Assumption 1: corners must fix the "
                  "substructure's zero-energy modes)",
                  AMB_EASSUMPTION);

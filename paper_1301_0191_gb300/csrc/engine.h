@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "common.h"
+#include "timers.h"
 #include "kernels.h"
 #include "level.h"
 #include "topology.h"
@@ -25,43 +26,6 @@ struct PairReportH {
   int level, s, t, n_computed, n_selected, n_rows, converged, iterations;
   std::vector<double> lambda;
   double residual = 0.0;
-};
-
-struct Timers {
-  double phase_ms[8] = {0};
-  double fam_ms[AMB_FAM_N] = {0};
-  int64_t fam_launches[AMB_FAM_N] = {0};
-  double fam_flops[AMB_FAM_N] = {0};
-  double fam_bytes[AMB_FAM_N] = {0};
-};
-
-// Event pair around a kernel family section (only when timing is enabled).
-struct FamTimer {
-  cudaStream_t st;
-  Timers* tm;
-  int fam;
-  bool on;
-  cudaEvent_t a = nullptr, b = nullptr;
-  int64_t l0;
-  FamTimer(cudaStream_t s, Timers* t, int f, bool enabled) : st(s), tm(t), fam(f), on(enabled), l0(g_launches) {
-    if (on) {
-      cudaEventCreate(&a);
-      cudaEventCreate(&b);
-      cudaEventRecord(a, st);
-    }
-  }
-  ~FamTimer() {
-    tm->fam_launches[fam] += g_launches - l0;
-    if (on) {
-      cudaEventRecord(b, st);
-      cudaEventSynchronize(b);
-      float ms = 0;
-      cudaEventElapsedTime(&ms, a, b);
-      tm->fam_ms[fam] += ms;
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-  }
 };
 
 class EngineBase {
