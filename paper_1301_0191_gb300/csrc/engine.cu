@@ -378,17 +378,32 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   gemm_batched<T>(st, ring, d, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Z3), dptr<T>(L.Psi));
   psi_corner_rows<T>(st, dptr<T>(L.Psi), dptr<int64_t>(L.par), ns, imax(L.nc));
   // Ac = Psi^T S Psi
-  d.clear();
-  for (int s = 0; s < ns; ++s)
-    d.push_back(GemmDesc{L.ng[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
-                         std::max(L.ng[s], 1), L.pS.off[s], L.pPsi.off[s], pT1.off[s]});
-  gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(L.S), dptr<T>(L.Psi), dptr<T>(T1));
-  d.clear();
-  for (int s = 0; s < ns; ++s)
-    d.push_back(GemmDesc{L.nc[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
-                         std::max(L.nc[s], 1), L.pPsi.off[s], pT1.off[s], pT2.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(T1), dptr<T>(T2));
-  coarse_to_double<T>(st, dptr<double>(L.Ac), dptr<T>(T2), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns, imax(L.nc));
+  std::vector<GemmDesc> d1, d2;
+  for (int s = 0; s < ns; ++s) {
+    d1.push_back(GemmDesc{L.ng[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
+                          std::max(L.ng[s], 1), L.pS.off[s], L.pPsi.off[s], pT1.off[s]});
+    d2.push_back(GemmDesc{L.nc[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
+                          std::max(L.nc[s], 1), L.pPsi.off[s], pT1.off[s], pT2.off[s]});
+  }
+  DevBuf PsiD, T1d, T2d;
+  if constexpr (std::is_same<T, float>::value) {
+    // FP32 form: S Psi = C^T(-mu) is small where S and Psi are not (it cancels
+    // on every unconstrained dof), so both products use the extended FP32-pair
+    // accumulation over the FP32 factors and give FP64 results.
+    PsiD.alloc(L.pPsi.total * sizeof(double));
+    T1d.alloc(pT1.total * sizeof(double));
+    T2d.alloc(pT2.total * sizeof(double));
+    convert<double, float>(st, dptr<double>(PsiD), dptr<float>(L.Psi), L.pPsi.total);
+    gemm_batched<double, float>(st, ring, d1, 0, 1.0, 0.0, dptr<float>(L.S), dptr<double>(PsiD), dptr<double>(T1d));
+    gemm_batched<double, float>(st, ring, d2, G_TRANS_A, 1.0, 0.0, dptr<float>(L.Psi), dptr<double>(T1d),
+                                dptr<double>(T2d));
+    coarse_to_double<double>(st, dptr<double>(L.Ac), dptr<double>(T2d), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns,
+                             imax(L.nc));
+  } else {
+    gemm_batched<T>(st, ring, d1, 0, one, zero, dptr<T>(L.S), dptr<T>(L.Psi), dptr<T>(T1));
+    gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(T1), dptr<T>(T2));
+    coarse_to_double<T>(st, dptr<double>(L.Ac), dptr<T>(T2), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns, imax(L.nc));
+  }
   AMB_CUDA(cudaStreamSynchronize(st));
 }
 

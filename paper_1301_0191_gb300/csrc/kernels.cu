@@ -217,6 +217,19 @@ void psi_corner_rows(cudaStream_t st, T* Psi, const int64_t* par, int ns, int ma
   AMB_LAUNCHED();
 }
 
+template <typename To, typename Ti>
+__global__ void k_convert(To* out, const Ti* in, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (To)in[i];
+}
+template <typename To, typename Ti>
+void convert(cudaStream_t st, To* out, const Ti* in, int64_t n) {
+  if (n <= 0) return;
+  k_convert<To, Ti><<<blocks(n), 256, 0, st>>>(out, in, n);
+  AMB_LAUNCHED();
+}
+template void convert<double, float>(cudaStream_t, double*, const float*, int64_t);
+
 template <typename T>
 __global__ void k_coarse_to_double(double* Ac, const T* T1, const int64_t* toff, const int64_t* par) {
   const int s = blockIdx.y;
@@ -369,46 +382,67 @@ void sub_vec(cudaStream_t st, double* out, const double* a, const double* b, int
   AMB_LAUNCHED();
 }
 
-// Sturm-sequence bisection on the Lanczos tridiagonal T of CG:
-// T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j.
-__device__ int sturm_count(const double* alphas, const double* betas, int k, double x) {
+// Extreme eigenvalues of the Lanczos tridiagonal T of CG,
+// T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} = sqrt(beta_j)/alpha_j,
+// by Sturm-sequence multisection: the diagonal and the squared off-diagonal
+// are formed once in shared memory; each half-warp narrows one extreme by
+// counting at 16 interior points per round (17-fold per round).
+__device__ int sturm_count(const double* dg, const double* e2, int k, double x) {
   int cnt = 0;
   double q = 1.0;
   for (int j = 0; j < k; ++j) {
-    double d = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
-    double e2 = 0.0;
-    if (j > 0) {
-      double e = sqrt(betas[j - 1]) / alphas[j - 1];
-      e2 = e * e;
-    }
-    q = d - x - (j > 0 ? e2 / q : 0.0);
+    q = dg[j] - x - (j > 0 ? e2[j] / q : 0.0);
     if (q == 0.0) q = -1e-300;
     if (q < 0.0) ++cnt;
   }
   return cnt;
 }
 __global__ void k_tridiag_extremes(double* out, const double* alphas, const double* betas, int k) {
-  if (threadIdx.x > 1) return;
-  // Gershgorin bounds
-  double lo = 1e300, hi = -1e300;
-  for (int j = 0; j < k; ++j) {
-    double d = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
-    double r = 0.0;
-    if (j > 0) r += sqrt(betas[j - 1]) / alphas[j - 1];
-    if (j < k - 1) r += sqrt(betas[j]) / alphas[j];
-    lo = fmin(lo, d - r);
-    hi = fmax(hi, d + r);
+  extern __shared__ double tsh[];
+  double* dg = tsh;
+  double* e2 = tsh + k;
+  __shared__ double bnd[2];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    dg[j] = 1.0 / alphas[j] + (j > 0 ? betas[j - 1] / alphas[j - 1] : 0.0);
+    e2[j] = j > 0 ? betas[j - 1] / (alphas[j - 1] * alphas[j - 1]) : 0.0;
   }
-  const int target = threadIdx.x == 0 ? 1 : k;   // count of eigenvalues < x reaching target
-  double a = lo, b = hi;
-  for (int it = 0; it < 200; ++it) {
-    double m = 0.5 * (a + b);
-    if (sturm_count(alphas, betas, k, m) >= target) b = m; else a = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {   // Gershgorin bounds
+    double lo = 1e300, hi = -1e300;
+    for (int j = 0; j < k; ++j) {
+      double r = 0.0;
+      if (j > 0) r += sqrt(e2[j]);
+      if (j < k - 1) r += sqrt(e2[j + 1]);
+      lo = fmin(lo, dg[j] - r);
+      hi = fmax(hi, dg[j] + r);
+    }
+    bnd[0] = lo;
+    bnd[1] = hi;
   }
-  out[threadIdx.x] = 0.5 * (a + b);
+  __syncthreads();
+  const int half = threadIdx.x >> 4, l = threadIdx.x & 15;   // half-warp 0: smallest, 1: largest
+  const int target = half == 0 ? 1 : k;   // count of eigenvalues below x reaching target
+  const unsigned mask = half == 0 ? 0x0000ffffu : 0xffff0000u;
+  double a = bnd[0], b = bnd[1];
+  for (int round = 0; round < 40 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++round) {
+    const double x = a + (b - a) * (l + 1) / 17.0;
+    const int hit = sturm_count(dg, e2, k, x) >= target;
+    // the first point reaching the target brackets the eigenvalue
+    const unsigned bal = __ballot_sync(mask, hit) >> (half * 16);
+    const int f = bal ? __ffs(bal) - 1 : 16;   // index of that point (16: none)
+    const double na = f == 0 ? a : a + (b - a) * f / 17.0;
+    const double nb = f == 16 ? b : a + (b - a) * (f + 1) / 17.0;
+    a = na;
+    b = nb;
+  }
+  if (l == 0) out[half] = 0.5 * (a + b);
 }
 void tridiag_extremes(cudaStream_t st, double* out, const double* alphas, const double* betas, int k) {
-  k_tridiag_extremes<<<1, 32, 0, st>>>(out, alphas, betas, k);
+  if (k <= 0) return;
+  const size_t smem = (size_t)2 * k * sizeof(double);
+  AMB_CHECK(smem <= 200 * 1024, AMB_EINVAL, "Lanczos tridiagonal too long for the condition estimate");
+  AMB_CUDA(cudaFuncSetAttribute(k_tridiag_extremes, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_tridiag_extremes<<<1, 32, smem, st>>>(out, alphas, betas, k);
   AMB_LAUNCHED();
 }
 

@@ -58,6 +58,10 @@ void sub_identity(cudaStream_t st, T* W1, const int64_t* woff, const int64_t* pa
 template <typename T>
 void psi_corner_rows(cudaStream_t st, T* Psi, const int64_t* par, int ns, int max_nc);
 // Ac (double, symmetrized) from T1 = Psi^T S Psi (T, nc x nc, ld nc at toff)
+// elementwise type conversion
+template <typename To, typename Ti>
+void convert(cudaStream_t st, To* out, const Ti* in, int64_t n);
+
 template <typename T>
 void coarse_to_double(cudaStream_t st, double* Ac, const T* T1, const int64_t* toff, const int64_t* par, int ns,
                       int max_nc);

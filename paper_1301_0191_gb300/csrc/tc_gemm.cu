@@ -249,26 +249,29 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
       if (!role_wait(smem_u32(&tfull), tl & 1, &abort_sh, g.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float acc[kTN];
+      // drain: per 16-column slice, the four accumulators' loads go out together, one wait
 #pragma unroll
-      for (int q = 0; q < kTN; ++q) acc[q] = 0.f;
-#pragma unroll
-      for (int cb = 0; cb < kTN / 32; ++cb) {
+      for (int h = 0; h < kTN / 16; ++h) {
+        uint32_t r[4][16];
 #pragma unroll
         for (int a = 0; a < 4; ++a) {
-          if (a < 3 && a >= nsteps) continue;
-          uint32_t r[32];
-          const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTN + cb * 32);
+          const uint32_t ta = tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTN + h * 16);
           asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
-              "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-                "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[a][0]), "=r"(r[a][1]), "=r"(r[a][2]), "=r"(r[a][3]), "=r"(r[a][4]), "=r"(r[a][5]),
+                "=r"(r[a][6]), "=r"(r[a][7]), "=r"(r[a][8]), "=r"(r[a][9]), "=r"(r[a][10]), "=r"(r[a][11]),
+                "=r"(r[a][12]), "=r"(r[a][13]), "=r"(r[a][14]), "=r"(r[a][15])
               : "r"(ta));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        // accumulators not yet written (fewer than three K = 8 steps) hold no data
 #pragma unroll
-          for (int q = 0; q < 32; ++q) acc[cb * 32 + q] += __uint_as_float(r[q]);
+        for (int q = 0; q < 16; ++q) {
+          float v = __uint_as_float(r[3][q]);
+          if (nsteps > 0) v += __uint_as_float(r[0][q]);
+          if (nsteps > 1) v += __uint_as_float(r[1][q]);
+          if (nsteps > 2) v += __uint_as_float(r[2][q]);
+          acc[h * 16 + q] = v;
         }
       }
       // TMEM back to the MMA warp before the C traffic
@@ -278,22 +281,22 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
       const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
       if (i < d.m) {
         float* row = g.c + d.c + i;
+        // 64 columns at a time: all loads first, then the stores
 #pragma unroll
-        for (int cb = 0; cb < kTN / 32; ++cb) {
-          // all loads of the chunk first, then the stores
-          const int j0 = tj * kTN + cb * 32;
-          float cv[32];
+        for (int cb = 0; cb < kTN / 64; ++cb) {
+          const int j0 = tj * kTN + cb * 64;
+          float cv[64];
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
+          for (int q = 0; q < 64; ++q) {
             const int j = j0 + q;
             const bool w = j < d.n && !(d.lower && j > i);
             cv[q] = (w && g.beta != 0.f) ? __ldcg(row + (int64_t)j * d.ldc) : 0.f;
           }
 #pragma unroll
-          for (int q = 0; q < 32; ++q) {
+          for (int q = 0; q < 64; ++q) {
             const int j = j0 + q;
             if (j >= d.n || (d.lower && j > i)) continue;
-            row[(int64_t)j * d.ldc] = fmaf(g.beta, cv[q], g.alpha * acc[cb * 32 + q]);
+            row[(int64_t)j * d.ldc] = fmaf(g.beta, cv[q], g.alpha * acc[cb * 64 + q]);
           }
         }
       }
