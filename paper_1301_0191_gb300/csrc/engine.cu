@@ -31,6 +31,8 @@ void Engine<T>::check_status(const char* what, int code) {
     AMB_CUDA(cudaMemsetAsync(status.p, 0, 4 * sizeof(int), st));
     if (h[0] == AMB_ETIMEOUT)
       throw Error(AMB_ETIMEOUT, std::string(what) + ": a bounded wait inside a kernel ran out");
+    if (h[0] == AMB_ENOCONV)
+      throw Error(AMB_ENOCONV, std::string(what) + ": a dense symmetric eigensolver exceeded its sweep limit");
     throw Error(code ? code : h[0], std::string(what) + ": non-positive pivot in substructure " +
                                         std::to_string(h[1]) + " at column " + std::to_string(h[2]));
   }
