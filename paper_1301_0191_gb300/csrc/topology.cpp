@@ -462,7 +462,11 @@ LevelTopo build_level_next(const LevelTopo& prev, const int32_t* parent, int n_s
     N.subs.insert(N.subs.end(), ps.begin(), ps.end());
     N.soff.push_back((int)N.subs.size());
     N.tags[o] = ob.tags;
-    N.eligible[o] = ob.kind == OBJ_CORNER;
+    // a level-i corner is a box vertex of level i+1 when every direction in
+    // which it is not on the domain boundary is a cut of level i+1, i.e. when
+    // 2^(3 - #boundary bits) level-(i+1) substructures share it
+    const int nb = __builtin_popcount((unsigned)ob.tags & 63u);
+    N.eligible[o] = ob.kind == OBJ_CORNER && nb <= 3 && (int)ps.size() == (1 << (3 - nb));
     for (size_t q = 0; q < ob.dofs.size(); ++q) {
       N.dofs.push_back(ob.first + (int64_t)q);
       N.comps.push_back(ob.comps[q]);

@@ -6,8 +6,11 @@
 // tags) class contains that node alone; for box partitions these are the
 // vertices of the box grid (every coordinate on a cut plane or on the
 // domain boundary), minus Dirichlet nodes.  On level i >= 2 the nodes are
-// the coarse objects of level i-1 and only level-(i-1) corners may become
-// corners.
+// the coarse objects of level i-1; a level-(i-1) corner becomes a corner
+// when it is a vertex of the level-i box grid: with b boundary bits, it is
+// shared by 2^(3-b) level-i substructures.  (A level-(i-1) corner on the
+// domain boundary inside a level-i face is alone in its class, because the
+// face objects around it carry no boundary bits, but it is no box vertex.)
 #pragma once
 
 #include <array>

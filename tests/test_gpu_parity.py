@@ -139,19 +139,44 @@ def test_config1_end_to_end(B):
     ctx.close()
 
 
-def test_three_levels(B):
+@pytest.mark.parametrize("dpn", [1, 3])
+def test_three_levels(B, dpn):
+    """Three levels (4x2x1 substructures in 2x1x1 level-2 groups): the level-2
+    corners are the level-1 corners on level-2 box vertices; coarse objects,
+    pair eigenvalues and selections on both levels match the oracle."""
     groups = [np.array([0, 2, 4]), np.array([0, 2]), np.array([0, 1])]
-    prob = ai.toy(3, 1, 41, split=(4, 2, 1), levels=3, groups=groups, sigma=1.0, tau=2.0)
+    prob = ai.toy(3, dpn, 41, split=(4, 2, 1), levels=3, groups=groups, sigma=1.0, tau=2.0)
     ctx = _ctx(B, prob, lobpcg_tol=1e-8, lobpcg_maxit=300)
     f = ctx.load_vector(prob.body)
     u, info = ctx.solve(f)
+    rep = ctx.report()
     h, res, f_free = solver.solve(prob)
     free = _free(prob)
     ud = spla.spsolve(h.ops[0].tocsc(), f_free)
     assert np.linalg.norm(u[free] - ud) <= 1e-6 * np.linalg.norm(ud)
     assert abs(info.iterations - res.its) <= 1, (info.iterations, res.its)
+    same_selection = True
+    for lev in (1, 2):
+        li, ol, orep = ctx.level_info(lev), h.levels[lev - 1], h.reports[lev - 1]
+        assert li.n_dofs == ol.n
+        assert li.n_corner_nodes == int(ol.node_corner.sum())
+        assert li.n_edges == len(ol.edges) and li.n_faces == len(ol.faces)
+        gp = {(p["s"], p["t"]): p for p in rep["pairs"] if p["level"] == lev}
+        assert sorted(gp) == sorted((int(s), int(t)) for s, t in orep.pairs)
+        for (s, t), lo, k_o in zip(orep.pairs, orep.lam, orep.n_selected):
+            pr = gp[(int(s), int(t))]
+            assert abs(pr["n_selected"] - k_o) <= 1
+            if same_selection:
+                lo = np.sort(np.asarray(lo))[::-1]
+                for i in range(min(len(lo), len(pr["lam"]), pr["n_selected"] + 1)):
+                    if lo[i] >= 0.1 * prob.tau:
+                        assert abs(pr["lam"][i] - lo[i]) <= 1e-4 * lo[i], (lev, s, t, i, pr["lam"][i], lo[i])
+        # level-2 elements carry the level-1 adaptive rows: compare their
+        # eigenvalues only when the level-1 selections agree
+        same_selection = same_selection and all(
+            gp[(int(s), int(t))]["n_selected"] == k_o for (s, t), k_o in zip(orep.pairs, orep.n_selected))
     li2 = ctx.level_info(2)
-    assert li2.n_subs == 2 and li2.n_dofs == h.levels[1].n
+    assert li2.n_subs == 2
     ctx.close()
 
 
