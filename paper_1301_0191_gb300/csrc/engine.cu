@@ -269,12 +269,15 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   L.Cd.alloc(L.pCd.total * sizeof(T));
   L.Y.alloc(L.pY.total * sizeof(T));
   L.Ginv.alloc(L.pG.total * sizeof(T));
+  L.Yd.alloc(L.pY.total * sizeof(double));
+  L.Ginvd.alloc(L.pG.total * sizeof(double));
+  L.zDd.alloc(L.vD.total * sizeof(double));
+  L.qCPd.alloc(L.vCP.total * sizeof(double));
+  L.lCPd.alloc(L.vCP.total * sizeof(double));
   L.Psi.alloc(L.pPsi.total * sizeof(T));
   L.Ac.alloc(L.pAc.total * sizeof(double));
   L.cC.alloc(L.vC.total * sizeof(T));
   L.ucC.alloc(L.vC.total * sizeof(T));
-  L.qCP.alloc(L.vCP.total * sizeof(T));
-  L.lCP.alloc(L.vCP.total * sizeof(T));
   L.rcg.alloc(tp.n_coarse * sizeof(double));
   L.ucg.alloc(tp.n_coarse * sizeof(double));
   upload_par(L);
@@ -316,70 +319,98 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   pW.build(sW);
   pT1.build(sT1);
   pT2.build(sT2);
-  DevBuf G, Z2, Z3, W1, Lam, T1, T2, dz, dw, dt2;
-  G.alloc(L.pG.total * sizeof(T));
+  // The constraint space is carried in FP64 in both forms: with strong
+  // coefficient contrast G = C_D S_DD^{-1} C_D^T is very ill-conditioned, and
+  // FP32 rounding of G (or of its inverse) makes the constrained Neumann
+  // solve non-SPD.  Products over the factor-precision L_D use the extended
+  // FP32-pair accumulation in the FP32 form (gemm_batched<double, T>).
+  DevBuf Gd, CdD, Z2, Z2d, Z3d, W1d, Lamd, PsiD, T1d, T2d, dz, dw, dt2;
+  Gd.alloc(L.pG.total * sizeof(double));
   Z2.alloc(pZ.total * sizeof(T));
-  Z3.alloc(pZ.total * sizeof(T));
-  W1.alloc(pW.total * sizeof(T));
-  Lam.alloc(pW.total * sizeof(T));
-  T1.alloc(pT1.total * sizeof(T));
-  T2.alloc(pT2.total * sizeof(T));
+  Z3d.alloc(pZ.total * sizeof(double));
+  W1d.alloc(pW.total * sizeof(double));
+  Lamd.alloc(pW.total * sizeof(double));
+  PsiD.alloc(L.pPsi.total * sizeof(double));
+  T1d.alloc(pT1.total * sizeof(double));
+  T2d.alloc(pT2.total * sizeof(double));
   upload(dz, pZ.off, st);
   upload(dw, pW.off, st);
   upload(dt2, pT2.off, st);
-  const T one = T(1), zero = T(0);
+  // B operands of the mixed products must be FP64
+  const double* cdd = nullptr;
+  const double* z2d = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    cdd = dptr<double>(L.Cd);
+    z2d = dptr<double>(Z2);
+  } else {
+    CdD.alloc(L.pCd.total * sizeof(double));
+    Z2d.alloc(pZ.total * sizeof(double));
+    convert<double, T>(st, dptr<double>(CdD), dptr<T>(L.Cd), L.pCd.total);
+    cdd = dptr<double>(CdD);
+    z2d = dptr<double>(Z2d);
+  }
   std::vector<GemmDesc> d;
-  // Y = L_D^{-1} C_D^T
+  // Yd = L_D^{-1} C_D^T
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.ncp[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.ncp[s], 1),
                          std::max(L.nd[s], 1), L.pLD.off[s], L.pCd.off[s], L.pY.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRI_A_LOWER | G_TRANS_B, one, zero, dptr<T>(L.LinvD), dptr<T>(L.Cd), dptr<T>(L.Y));
-  // G = Y^T Y
+  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER | G_TRANS_B, 1.0, 0.0, dptr<T>(L.LinvD), cdd, dptr<double>(L.Yd));
+  // G = Yd^T Yd (FP64, positive semi-definite by construction), Ginvd = G^{-1}
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.ncp[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ncp[s], 1), L.pY.off[s], L.pY.off[s], L.pG.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(L.Y), dptr<T>(G));
+  gemm_batched<double>(st, ring, d, G_TRANS_A, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(L.Yd), dptr<double>(Gd));
   DevBuf dgo;
   upload(dgo, L.pG.off, st);
-  small_spd_inverse<T>(st, dptr<T>(L.Ginv), dptr<T>(G), dptr<int64_t>(dgo), dptr<int64_t>(L.par), ns, imax(L.ncp),
-                       dptr<int>(status));
+  small_spd_inverse<double>(st, dptr<double>(L.Ginvd), dptr<double>(Gd), dptr<int64_t>(dgo), dptr<int64_t>(L.par), ns,
+                            imax(L.ncp), dptr<int>(status));
   check_status("constraint Schur complement C_D S_DD^{-1} C_D^T (dependent constraint rows)", AMB_EASSUMPTION);
+  // factor-precision copies for the pair preconditioner of LOBPCG
+  convert<T, double>(st, dptr<T>(L.Y), dptr<double>(L.Yd), L.pY.total);
+  convert<T, double>(st, dptr<T>(L.Ginv), dptr<double>(L.Ginvd), L.pG.total);
   // R = [-S_Dc | 0]; Z3 = L_D^{-1} R
   psi_rhs<T>(st, dptr<T>(Z2), dptr<int64_t>(dz), dptr<T>(L.S), dptr<int64_t>(L.par), ns, imax(L.nd), imax(L.nc));
+  if constexpr (!std::is_same<T, double>::value)
+    convert<double, T>(st, dptr<double>(Z2d), dptr<T>(Z2), pZ.total);
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.nd[s], 1), L.pLD.off[s], pZ.off[s], pZ.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Z2), dptr<T>(Z3));
-  // W1 = Y^T Z3 - [0 | I]
+  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER, 1.0, 0.0, dptr<T>(L.LinvD), z2d, dptr<double>(Z3d));
+  // W1 = Yd^T Z3 - [0 | I]
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ncp[s], 1), L.pY.off[s], pZ.off[s], pW.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Z3), dptr<T>(W1));
-  sub_identity<T>(st, dptr<T>(W1), dptr<int64_t>(dw), dptr<int64_t>(L.par), ns, imax(L.ncp));
+  gemm_batched<double>(st, ring, d, G_TRANS_A, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(Z3d), dptr<double>(W1d));
+  sub_identity<double>(st, dptr<double>(W1d), dptr<int64_t>(dw), dptr<int64_t>(L.par), ns, imax(L.ncp));
   // Lam = G^{-1} W1
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.nc[s], L.ncp[s], std::max(L.ncp[s], 1), std::max(L.ncp[s], 1),
                          std::max(L.ncp[s], 1), L.pG.off[s], pW.off[s], pW.off[s]});
-  gemm_batched<T>(st, ring, d, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(W1), dptr<T>(Lam));
-  // Z3 -= Y Lam
+  gemm_batched<double>(st, ring, d, 0, 1.0, 0.0, dptr<double>(L.Ginvd), dptr<double>(W1d), dptr<double>(Lamd));
+  // Z3 -= Yd Lam
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.nc[s], L.ncp[s], std::max(L.nd[s], 1), std::max(L.ncp[s], 1),
                          std::max(L.nd[s], 1), L.pY.off[s], pW.off[s], pZ.off[s]});
-  gemm_batched<T>(st, ring, d, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Lam), dptr<T>(Z3));
-  // Psi_D = L_D^{-T} Z3 ; Psi_c = [I 0]
+  gemm_batched<double>(st, ring, d, 0, -1.0, 1.0, dptr<double>(L.Yd), dptr<double>(Lamd), dptr<double>(Z3d));
+  // Psi_D = L_D^{-T} Z3 ; Psi_c = [I 0]  (FP64; the factor-precision copy feeds Algorithm 1)
+  AMB_CUDA(cudaMemsetAsync(PsiD.p, 0, L.pPsi.total * sizeof(double), st));
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ng[s], 1), L.pLD.off[s], pZ.off[s], L.pPsi.off[s]});
-  gemm_batched<T>(st, ring, d, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Z3), dptr<T>(L.Psi));
-  psi_corner_rows<T>(st, dptr<T>(L.Psi), dptr<int64_t>(L.par), ns, imax(L.nc));
-  // Ac = Psi^T S Psi
+  gemm_batched<double, T>(st, ring, d, G_TRANS_A | G_TRI_A_UPPER, 1.0, 0.0, dptr<T>(L.LinvD), dptr<double>(Z3d),
+                          dptr<double>(PsiD));
+  psi_corner_rows<double>(st, dptr<double>(PsiD), dptr<int64_t>(L.par), ns, imax(L.nc));
+  convert<T, double>(st, dptr<T>(L.Psi), dptr<double>(PsiD), L.pPsi.total);
+  // Ac = Psi^T S Psi: S Psi = C^T(-mu) is small where S and Psi are not (it
+  // cancels on every unconstrained dof): S Psi with the FP64 Psi and extended
+  // accumulation over S, then Psi^T (S Psi) in FP64
   std::vector<GemmDesc> d1, d2;
   for (int s = 0; s < ns; ++s) {
     d1.push_back(GemmDesc{L.ng[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
@@ -387,25 +418,10 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
     d2.push_back(GemmDesc{L.nc[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
                           std::max(L.nc[s], 1), L.pPsi.off[s], pT1.off[s], pT2.off[s]});
   }
-  DevBuf PsiD, T1d, T2d;
-  if constexpr (std::is_same<T, float>::value) {
-    // FP32 form: S Psi = C^T(-mu) is small where S and Psi are not (it cancels
-    // on every unconstrained dof), so both products use the extended FP32-pair
-    // accumulation over the FP32 factors and give FP64 results.
-    PsiD.alloc(L.pPsi.total * sizeof(double));
-    T1d.alloc(pT1.total * sizeof(double));
-    T2d.alloc(pT2.total * sizeof(double));
-    convert<double, float>(st, dptr<double>(PsiD), dptr<float>(L.Psi), L.pPsi.total);
-    gemm_batched<double, float>(st, ring, d1, 0, 1.0, 0.0, dptr<float>(L.S), dptr<double>(PsiD), dptr<double>(T1d));
-    gemm_batched<double, float>(st, ring, d2, G_TRANS_A, 1.0, 0.0, dptr<float>(L.Psi), dptr<double>(T1d),
-                                dptr<double>(T2d));
-    coarse_to_double<double>(st, dptr<double>(L.Ac), dptr<double>(T2d), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns,
-                             imax(L.nc));
-  } else {
-    gemm_batched<T>(st, ring, d1, 0, one, zero, dptr<T>(L.S), dptr<T>(L.Psi), dptr<T>(T1));
-    gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(T1), dptr<T>(T2));
-    coarse_to_double<T>(st, dptr<double>(L.Ac), dptr<T>(T2), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns, imax(L.nc));
-  }
+  gemm_batched<double, T>(st, ring, d1, 0, 1.0, 0.0, dptr<T>(L.S), dptr<double>(PsiD), dptr<double>(T1d));
+  gemm_batched<double>(st, ring, d2, G_TRANS_A, 1.0, 0.0, dptr<double>(PsiD), dptr<double>(T1d), dptr<double>(T2d));
+  coarse_to_double<double>(st, dptr<double>(L.Ac), dptr<double>(T2d), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns,
+                           imax(L.nc));
   AMB_CUDA(cudaStreamSynchronize(st));
 }
 
@@ -523,15 +539,24 @@ void Engine<T>::apply_level(int i, const double* r, double* u) {
   d.clear();
   for (int s = 0; s < ns; ++s) d.push_back(mk(L.nd[s], L.nd[s], L.nd[s], L.pLD.off[s], L.vG.off[s], L.vD.off[s]));
   gemv_batched<T>(st, ring, d, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(L.gG), dptr<T>(L.zD));
+  // G correction in FP64 (constraint space): q = Yd^T z; l = Ginvd q; z -= Yd l
+  double* zd = nullptr;
+  if constexpr (std::is_same<T, double>::value) {
+    zd = dptr<double>(L.zD);
+  } else {
+    zd = dptr<double>(L.zDd);
+    convert<double, T>(st, zd, dptr<T>(L.zD), L.vD.total);
+  }
   d.clear();
   for (int s = 0; s < ns; ++s) d.push_back(mk(L.nd[s], L.ncp[s], L.nd[s], L.pY.off[s], L.vD.off[s], L.vCP.off[s]));
-  gemv_batched<T>(st, ring, d, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(L.zD), dptr<T>(L.qCP));
+  gemv_batched<double>(st, ring, d, G_TRANS_A, 1.0, 0.0, dptr<double>(L.Yd), zd, dptr<double>(L.qCPd));
   d.clear();
   for (int s = 0; s < ns; ++s) d.push_back(mk(L.ncp[s], L.ncp[s], L.ncp[s], L.pG.off[s], L.vCP.off[s], L.vCP.off[s]));
-  gemv_batched<T>(st, ring, d, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(L.qCP), dptr<T>(L.lCP));
+  gemv_batched<double>(st, ring, d, 0, 1.0, 0.0, dptr<double>(L.Ginvd), dptr<double>(L.qCPd), dptr<double>(L.lCPd));
   d.clear();
   for (int s = 0; s < ns; ++s) d.push_back(mk(L.nd[s], L.ncp[s], L.nd[s], L.pY.off[s], L.vCP.off[s], L.vD.off[s]));
-  gemv_batched<T>(st, ring, d, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(L.lCP), dptr<T>(L.zD));
+  gemv_batched<double>(st, ring, d, 0, -1.0, 1.0, dptr<double>(L.Yd), dptr<double>(L.lCPd), zd);
+  if constexpr (!std::is_same<T, double>::value) convert<T, double>(st, dptr<T>(L.zD), zd, L.vD.total);
   AMB_CUDA(cudaMemsetAsync(L.vGw.p, 0, L.vG.total * sizeof(T), st));
   d.clear();
   for (int s = 0; s < ns; ++s) d.push_back(mk(L.nd[s], L.nd[s], L.nd[s], L.pLD.off[s], L.vD.off[s], L.vG.off[s]));

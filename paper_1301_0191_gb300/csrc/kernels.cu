@@ -229,6 +229,8 @@ void convert(cudaStream_t st, To* out, const Ti* in, int64_t n) {
   AMB_LAUNCHED();
 }
 template void convert<double, float>(cudaStream_t, double*, const float*, int64_t);
+template void convert<float, double>(cudaStream_t, float*, const double*, int64_t);
+template void convert<double, double>(cudaStream_t, double*, const double*, int64_t);
 
 template <typename T>
 __global__ void k_coarse_to_double(double* Ac, const T* T1, const int64_t* toff, const int64_t* par) {

@@ -44,6 +44,11 @@ struct LevelData {
   Pools pM, pS, pLI, pLD, pCd, pY, pG, pPsi, pAc;
   Pools vI, vG, vD, vC, vCP;   // flattened per-sub vector offsets
   DevBuf M, S, LinvI, LinvD, Cd, Y, Ginv, Psi, Ac;
+  // FP64 constraint space in both forms: Yd = L_D^{-1} C_D^T and Ginvd =
+  // (Yd^T Yd)^{-1}; Y and Ginv above are factor-precision copies used only
+  // by the pair preconditioner of LOBPCG
+  DevBuf Yd, Ginvd;
+  DevBuf zDd, qCPd, lCPd;      // double work vectors of the G correction
   DevBuf diagG;                // double, diag(K_GG) before elimination (sum n_g)
   DevBuf w;                    // T, stiffness-scaling weights (sum n_g)
   // index maps
@@ -54,8 +59,8 @@ struct LevelData {
   DevBuf rc;                   // int64 flat coarse entry -> global coarse id (sum n_c)
   DevBuf cown_off, cown_flat;  // int32 CSR: global coarse -> flat coarse entry
   int64_t n_iface = 0;
-  // work vectors (T): interior x2, interface x2, delta, coarse-nc x2, coarse-ncp x2
-  DevBuf xI, tI, gG, vGw, zD, cC, ucC, qCP, lCP;
+  // work vectors (T): interior x2, interface x2, delta, coarse-nc x2
+  DevBuf xI, tI, gG, vGw, zD, cC, ucC;
   DevBuf rB, rcg, ucg, uGd;    // double global vectors
   DevBuf par;                  // int64 ns x NPAR parameter table (kernels.h)
   std::vector<int64_t> par_h;

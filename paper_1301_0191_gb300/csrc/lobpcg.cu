@@ -300,6 +300,26 @@ __global__ void k_lob_sff(T* Sff, const T* S, const int64_t* qp, const int64_t* 
   for (int64_t a = threadIdx.x; a < nf; a += blockDim.x) dst[a] = src[pos[a]];
 }
 
+// Neumann solves of the pair preconditioner are batched per substructure:
+// the Delta rows of every active pair-side block of one substructure sit
+// side by side in a substructure-major buffer.  One map entry per pair-side:
+// its rows in the pair block (offset, leading dimension N) and its column
+// block in the substructure buffer (offset, leading dimension n_Delta).
+struct NeuMap {
+  int64_t pair_off, sub_off;
+  int32_t ldp, nd;
+};
+template <typename T>
+__global__ void k_lob_neu_move(T* dst, const T* src, const NeuMap* mp, int m, int to_sub) {
+  const NeuMap x = mp[blockIdx.y];
+  const int64_t n = (int64_t)x.nd * m;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % x.nd, c = idx / x.nd;
+    const int64_t po = x.pair_off + i + c * x.ldp, so = x.sub_off + i + c * x.nd;
+    if (to_sub) dst[so] = src[po]; else dst[po] = src[so];
+  }
+}
+
 // coarse gather/scatter of the pair coarse space
 template <typename T>
 __global__ void k_lob_cgather(T* C, const int64_t* qp, int m, const int32_t* cms, const int32_t* cmt) {
@@ -386,67 +406,95 @@ __global__ void __launch_bounds__(kJacobiThreads) k_pair_pinv(T* pinv, const int
 // The FP64 entries are split into FP32 pairs (x = x_h + x_l) and the dot
 // products carried in FP32 pairs (exact x_h*y_h by FMA, TwoSum, cross terms
 // into the low word): about 46 significant bits, at FP32 throughput.
+// Pass 1 (k_lob_gram_part): one CTA per (pair, kind, chunk of kGramRows
+// rows); a thread owns a 2 x 2 block of the upper triangle, so each staged
+// row costs two operand loads per two multiply-adds.  Pass 2
+// (k_lob_gram_sum) adds the chunks in order (the sums are deterministic).
+constexpr int kGramRows = 512;
+
+__device__ __forceinline__ void df_mac(float& h, float& l, float2 x, float2 y) {
+  const float pr = __fmul_rn(x.x, y.x);
+  const float e = fmaf(x.x, y.x, -pr);
+  const float s = __fadd_rn(h, pr);
+  const float bb = __fsub_rn(s, h);
+  const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(pr, bb));
+  h = s;
+  l = fmaf(x.x, y.y, fmaf(x.y, y.x, __fadd_rn(l, __fadd_rn(er, e))));
+}
+
 template <typename T>
-__global__ void k_lob_gram(double* G, const T* Qb, const int64_t* qp, int m, int w, const int* act) {
-  const int p = blockIdx.x, kind = blockIdx.y;
-  if (!act[p]) return;
+__global__ void k_lob_gram_part(double* part, const T* Qb, const int64_t* qp, int m, int w, const int* act,
+                                int nchunk) {
+  const int p = blockIdx.x, kind = blockIdx.y, ch = blockIdx.z;
+  double* out = part + (((int64_t)p * 2 + kind) * nchunk + ch) * (int64_t)w * w;
+  const int nb = (w + 1) / 2, nblk = nb * (nb + 1) / 2;
   const int64_t N = QP(p, Q_N);
-  const int m3 = 3 * m;
+  const int64_t rb = (int64_t)ch * kGramRows, re = min(N, rb + kGramRows);
+  if (!act[p] || rb >= re) {
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) out[idx] = 0.0;
+    return;
+  }
   const T* U = Qb + QP(p, Q_OQ);
   const T* Vb = U + (int64_t)(kind ? 6 * m : 3 * m) * N;
-  __shared__ float2 us[32][3 * AMB_MAX_EIG + 1], vs[32][3 * AMB_MAX_EIG + 1];
-  constexpr int NQ = (3 * AMB_MAX_EIG * (3 * AMB_MAX_EIG + 1) / 2 + 255) / 256;
-  float hi[NQ], lo[NQ];
-  int oa[NQ], ob[NQ];
-  const int nout = w * (w + 1) / 2;
-  for (int q = 0; q < NQ; ++q) {
-    hi[q] = lo[q] = 0.f;
-    const int o = threadIdx.x + q * blockDim.x;
-    int b = (int)((sqrtf(8.f * o + 1.f) - 1.f) * 0.5f);
-    while (b * (b + 1) / 2 > o) --b;
-    while ((b + 1) * (b + 2) / 2 <= o) ++b;
-    oa[q] = o - b * (b + 1) / 2;
-    ob[q] = b;
-  }
-  for (int64_t r0 = 0; r0 < N; r0 += 32) {
-    const int rn = (N - r0) < 32 ? (int)(N - r0) : 32;
-    for (int idx = threadIdx.x; idx < 32 * w; idx += blockDim.x) {
+  __shared__ float2 us[32][3 * AMB_MAX_EIG + 2], vs[32][3 * AMB_MAX_EIG + 2];
+  // 2 x 2 block (bi, bj), bi <= bj, from the triangular thread index
+  const int t = threadIdx.x;
+  int bj = (int)((sqrtf(8.f * t + 1.f) - 1.f) * 0.5f);
+  while (bj * (bj + 1) / 2 > t) --bj;
+  while ((bj + 1) * (bj + 2) / 2 <= t) ++bj;
+  const int bi = t - bj * (bj + 1) / 2;
+  const bool mine = t < nblk;
+  const int a0 = 2 * bi, b0 = 2 * bj;
+  float h[2][2] = {{0.f, 0.f}, {0.f, 0.f}}, l[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
+  const int wp = 2 * nb;   // staged columns (w rounded up to even; the extra one is zero)
+  for (int64_t r0 = rb; r0 < re; r0 += 32) {
+    const int rn = (re - r0) < 32 ? (int)(re - r0) : 32;
+    for (int idx = threadIdx.x; idx < 32 * wp; idx += blockDim.x) {
       const int r = idx % 32, c = idx / 32;
-      const double u = r < rn ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
-      const double v = r < rn ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
+      const bool in = r < rn && c < w;
+      const double u = in ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
+      const double v = in ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
       const float uh = (float)u, vh = (float)v;
       us[r][c] = make_float2(uh, (float)(u - (double)uh));
       vs[r][c] = make_float2(vh, (float)(v - (double)vh));
     }
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-      const int o = threadIdx.x + q * blockDim.x;
-      if (o >= nout) break;
-      const int a = oa[q], b = ob[q];
-      float h = hi[q], l = lo[q];
+    if (mine) {
       for (int r = 0; r < rn; ++r) {
-        const float2 x = us[r][a], y = vs[r][b];
-        const float pr = __fmul_rn(x.x, y.x);
-        const float e = fmaf(x.x, y.x, -pr);
-        const float s = __fadd_rn(h, pr);
-        const float bb = __fsub_rn(s, h);
-        const float er = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(pr, bb));
-        h = s;
-        l = fmaf(x.x, y.y, fmaf(x.y, y.x, __fadd_rn(l, __fadd_rn(er, e))));
+        const float2 x0 = us[r][a0], x1 = us[r][a0 + 1], y0 = vs[r][b0], y1 = vs[r][b0 + 1];
+        df_mac(h[0][0], l[0][0], x0, y0);
+        df_mac(h[0][1], l[0][1], x0, y1);
+        df_mac(h[1][0], l[1][0], x1, y0);
+        df_mac(h[1][1], l[1][1], x1, y1);
       }
-      hi[q] = h;
-      lo[q] = l;
     }
     __syncthreads();
   }
+  if (mine) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int a = a0 + i, b = b0 + j;
+        if (a < w && b < w && a <= b) out[a + b * w] = (double)h[i][j] + (double)l[i][j];
+      }
+  }
+}
+
+__global__ void k_lob_gram_sum(double* G, const double* part, const int64_t* qp, int m, int w, const int* act,
+                               int nchunk) {
+  const int p = blockIdx.x, kind = blockIdx.y;
+  if (!act[p]) return;
+  const int m3 = 3 * m;
+  const double* in = part + ((int64_t)p * 2 + kind) * nchunk * (int64_t)w * w;
   double* g = G + QP(p, Q_OGR) + (int64_t)kind * m3 * m3;
-  for (int q = 0; q < NQ; ++q) {
-    const int o = threadIdx.x + q * blockDim.x;
-    if (o >= nout) break;
-    const double v = (double)hi[q] + (double)lo[q];
-    g[oa[q] + ob[q] * m3] = v;
-    g[ob[q] + oa[q] * m3] = v;
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int a = idx % w, b = idx / w;
+    if (a > b) continue;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += in[(int64_t)c * w * w + idx];
+    g[a + b * m3] = s;
+    g[b + a * m3] = s;
   }
 }
 
@@ -810,10 +858,18 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   Jb.alloc(oJ * sizeof(V));
   Sff.alloc(oF * sizeof(T));
   Zb.alloc(oZ * sizeof(T));
+  DevBuf Xs;   // substructure-major Neumann right-hand sides and solutions
+  Xs.alloc(oZ * sizeof(T));
   Qc.alloc(oQc * sizeof(T));
   Cb.alloc(oC * sizeof(T));
   Pinv.alloc(oPi * sizeof(T));
   Gr.alloc(oGr * sizeof(double));
+  int64_t maxN0 = 0;
+  for (int p = 0; p < np; ++p) maxN0 = std::max(maxN0, qp[(size_t)p * Q_NPAIRF + Q_N]);
+  const int ngchunk = (int)std::max<int64_t>(1, (maxN0 + kGramRows - 1) / kGramRows);
+  AMB_CHECK(ngchunk < 65536, AMB_EINVAL, "pair space too large for the Gram kernels");
+  DevBuf Gpart;
+  Gpart.alloc((size_t)np * 2 * ngchunk * m3 * m3 * sizeof(double));
   Cc.alloc(oCc * sizeof(V));
   lam.alloc((size_t)np * m * sizeof(double));
   rn.alloc((size_t)np * m * sizeof(double));
@@ -924,38 +980,72 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     to_op(dptr<V>(Tp), Q_OT, 0);
     zero_block(dptr<T>(Oout), Q_OO, 0, m);
     std::vector<GemmDesc> d1, d2, d3, d4, d5, dc1, dc2, dpi;
+    // Neumann: per substructure, z = L_D^{-1} r_D; q = Y^T z; l = Ginv q;
+    // z -= Y l; out_D = L_D^{-T} z, on the active pair-sides side by side
+    std::vector<int> nsd(L.ns, 0);
+    for (int p = 0; p < np; ++p) {
+      if (!active[p]) continue;
+      ++nsd[qp[(size_t)p * Q_NPAIRF + Q_S]];
+      ++nsd[qp[(size_t)p * Q_NPAIRF + Q_T]];
+    }
+    std::vector<int64_t> xo(L.ns, 0), qo2(L.ns, 0);
+    int64_t ox = 0, oq = 0;
+    for (int s2 = 0; s2 < L.ns; ++s2) {
+      xo[s2] = ox;
+      qo2[s2] = oq;
+      ox += (int64_t)L.nd[s2] * m * nsd[s2];
+      oq += (int64_t)2 * L.ncp[s2] * m * nsd[s2];
+    }
+    std::vector<NeuMap> nmap;
+    std::vector<int> used(L.ns, 0);
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      if (!active[p]) continue;
+      for (int side = 0; side < 2; ++side) {
+        const int sub = (int)(side ? q[Q_T] : q[Q_S]);
+        const int64_t r0 = side ? q[Q_NS] : 0;
+        nmap.push_back(NeuMap{q[Q_OO] + r0, xo[sub] + (int64_t)used[sub] * m * L.nd[sub], (int)q[Q_N], L.nd[sub]});
+        ++used[sub];
+      }
+    }
+    for (int s2 = 0; s2 < L.ns; ++s2) {
+      if (nsd[s2] == 0 || L.nd[s2] == 0) continue;
+      const int nd = L.nd[s2], ncp = L.ncp[s2], wd = m * nsd[s2];
+      const int ldd = std::max(nd, 1), ldc = std::max(ncp, 1);
+      const int64_t zo = xo[s2], qo = qo2[s2];
+      d1.push_back(GemmDesc{nd, wd, nd, ldd, ldd, ldd, L.pLD.off[s2], zo, zo});
+      d2.push_back(GemmDesc{ncp, wd, nd, ldd, ldd, ldc, L.pY.off[s2], zo, qo});
+      d3.push_back(GemmDesc{ncp, wd, ncp, ldc, ldc, ldc, L.pG.off[s2], qo, qo + (int64_t)ncp * wd});
+      d4.push_back(GemmDesc{nd, wd, ncp, ldd, ldc, ldd, L.pY.off[s2], qo + (int64_t)ncp * wd, zo});
+      d5.push_back(GemmDesc{nd, wd, nd, ldd, ldd, ldd, L.pLD.off[s2], zo, zo});
+    }
+    if (!nmap.empty()) {
+      const NeuMap* dmap = static_cast<const NeuMap*>(ring.push(nmap.data(), nmap.size() * sizeof(NeuMap), st));
+      const unsigned gx = (unsigned)std::min<int64_t>(nblk((int64_t)imax(L.nd) * m), 64);
+      k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Xs), dptr<T>(Oin), dmap, m, 1);
+      AMB_LAUNCHED();
+      gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Xs), dptr<T>(Zb));
+      gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
+      gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
+      gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
+      gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), dptr<T>(Xs));
+      k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Oout), dptr<T>(Xs), dmap, m, 0);
+      AMB_LAUNCHED();
+    }
+    // coarse: c = Psi^T r per pair-side ; later out += Psi u
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
       if (!active[p]) continue;
       const int64_t N = q[Q_N];
-      int64_t zo = zoff[p], qo = qcoff[p];
       int64_t co = q[Q_OC];
       for (int side = 0; side < 2; ++side) {
         const int sub = (int)(side ? q[Q_T] : q[Q_S]);
-        const int nd = L.nd[sub], ncp = L.ncp[sub], nc = L.nc[sub], ng = L.ng[sub];
-        const int64_t r0 = side ? q[Q_NS] : 0;
-        const int64_t rin = q[Q_OO] + r0, rout = q[Q_OO] + r0;
-        const int ldd = std::max(nd, 1), ldc = std::max(ncp, 1);
-        // Neumann: z = L_D^{-1} r_D; qv = Y^T z; l = Ginv qv; z -= Y l; out_D = L_D^{-T} z
-        d1.push_back(GemmDesc{nd, m, nd, ldd, (int)N, ldd, L.pLD.off[sub], rin, zo});
-        d2.push_back(GemmDesc{ncp, m, nd, ldd, ldd, ldc, L.pY.off[sub], zo, qo});
-        d3.push_back(GemmDesc{ncp, m, ncp, ldc, ldc, ldc, L.pG.off[sub], qo, qo + (int64_t)ncp * m});
-        d4.push_back(GemmDesc{nd, m, ncp, ldd, ldc, ldd, L.pY.off[sub], qo + (int64_t)ncp * m, zo});
-        d5.push_back(GemmDesc{nd, m, nd, ldd, ldd, (int)N, L.pLD.off[sub], zo, rout});
-        // coarse: c = Psi^T r ; later out += Psi u
+        const int nc = L.nc[sub], ng = L.ng[sub];
+        const int64_t rin = q[Q_OO] + (side ? q[Q_NS] : 0);
         dc1.push_back(GemmDesc{nc, m, ng, std::max(ng, 1), (int)N, std::max(nc, 1), L.pPsi.off[sub], rin, co});
-        zo += (int64_t)nd * m;
-        qo += (int64_t)2 * ncp * m;
         co += (int64_t)nc * m;
       }
     }
-    // the S-side and T-side blocks share base pointers: Zb for z, Qc for q/l, Cb for coarse
-    gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Oin), dptr<T>(Zb));
-    gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
-    gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
-    gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
-    gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb),
-                    dptr<T>(Oout));
     gemm_batched<T>(st, ring, dc1, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(Oin), dptr<T>(Cb));
     k_lob_cgather<T><<<np, 256, 0, st>>>(dptr<T>(Cb), QPd, m, dptr<int32_t>(dcms), dptr<int32_t>(dcmt));
     AMB_LAUNCHED();
@@ -990,7 +1080,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     project(Q, Q_OQ, cout * m, m);
   };
   auto rayleigh_ritz = [&](int w) {
-    k_lob_gram<V><<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), Q, QPd, m, w, dptr<int>(act_d));
+    k_lob_gram_part<V><<<dim3(np, 2, ngchunk), 320, 0, st>>>(dptr<double>(Gpart), Q, QPd, m, w, dptr<int>(act_d),
+                                                            ngchunk);
+    AMB_LAUNCHED();
+    k_lob_gram_sum<<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), dptr<double>(Gpart), QPd, m, w, dptr<int>(act_d),
+                                               ngchunk);
     AMB_LAUNCHED();
     const int wl = w + (w & 1);
     const size_t smem = (size_t)(5 * wl * wl + wl) * sizeof(double);

@@ -2,6 +2,8 @@
 
     python tests/golden/make_golden.py 1 2      # config indices
 
+    python tests/golden/make_golden.py grad4     # compliance gradient of config 4
+
 For each workload: PCG iterations and condition estimate of the adaptive
 two-level method (Algorithm 3 + Algorithm 1, rtol 1e-8), adaptive rows and
 indicator per level (eq. cond-ind-mlevel), the number of coarse dofs, and
@@ -17,6 +19,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import amb_inputs as ai  # noqa: E402
+import numpy as np  # noqa: E402
+
+from oracle import gradient as og  # noqa: E402
 from oracle import solver  # noqa: E402
 
 
@@ -41,7 +46,37 @@ def golden(index):
     return out
 
 
+def gradient_golden(index=4, n_samples=512):
+    """Compliance Q = f^T u and its adjoint gradient dQ/dlog(kappa_e) (the
+    spec gradient: lambda = u) at seeded sample elements.  u comes from
+    the oracle's two-level BDDC + PCG without adaptive constraints at rtol
+    1e-12 (the gradient does not depend on the preconditioner; a sparse LU of
+    the 270,400-dof system takes far longer)."""
+    prob = ai.config(index)
+    t0 = time.perf_counter()
+    h, res, f = solver.solve(prob, rtol=1e-12, adaptive=False)
+    u = res.u
+    g = og.element_gradient(prob, u, u)
+    rng = np.random.default_rng(np.random.PCG64(104))
+    idx = np.sort(rng.choice(g.size, size=n_samples, replace=False))
+    out = {
+        "workload": prob.name, "config_index": index, "compliance": float(f @ u),
+        "pcg_iterations": int(res.its), "rel_residual": float(res.rel_res),
+        "sample_elements": [int(i) for i in idx], "gradient_samples": [float(x) for x in g[idx]],
+        "gradient_abs_max": float(np.abs(g).max()), "gradient_sum": float(g.sum()),
+        "oracle_seconds": time.perf_counter() - t0,
+        "source": "oracle/ (tests/golden/make_golden.py grad4)",
+    }
+    with open(os.path.join(HERE, f"config{index}_gradient.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+    return out
+
+
 if __name__ == "__main__":
     for a in sys.argv[1:] or ["1"]:
+        if a.startswith("grad"):
+            o = gradient_golden(int(a[4:]))
+            print(o["workload"], o["compliance"], o["pcg_iterations"], o["oracle_seconds"])
+            continue
         o = golden(int(a))
         print(o["workload"], o["pcg_iterations"], o["n_adaptive"], o["omega_level"])
