@@ -194,9 +194,11 @@ struct TrtriDesc {
   int64_t l, z;
   int32_t ld, zld, n, pad;
 };
+// status: the tensor-core products of the FP32 form report a bounded wait
+// that ran out there (AMB_ETIMEOUT); may be null for the FP64 form.
 template <typename T>
 void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriDesc>& d, const T* lbase,
-                       T* zbase, double* flops);
+                       T* zbase, double* flops, int* status = nullptr);
 
 constexpr int kNB = 64;   // Cholesky / triangular-inverse block size
 

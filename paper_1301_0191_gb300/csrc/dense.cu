@@ -851,24 +851,45 @@ template void partial_cholesky<double>(cudaStream_t, DescRing&, const std::vecto
 
 template <typename T>
 void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriDesc>& d, const T* lbase,
-                       T* zbase, double* flops) {
+                       T* zbase, double* flops, int* status) {
   int maxn = 0;
   for (const auto& x : d) maxn = std::max(maxn, x.n);
   for (int half = kNB; half < maxn; half *= 2) {
     const int b = 2 * half;
     std::vector<GemmDesc> sa, sb;
+    std::vector<TcGemm> ta, tb;
+    // FP32 form: merges with K >= the tensor-core chunk width run as 3xTF32
+    // tensor-core products (K in chunks, accumulated in FP32 through C)
+    const bool tc = std::is_same<T, float>::value && half >= kTcKMax;
     for (const auto& x : d) {
       for (int p0 = 0; p0 + half < x.n; p0 += b) {
         const int h = p0 + half;
         const int r2 = std::min(p0 + b, x.n) - h;
         const int c1 = half;
-        // Z12 (c1 x r2) := Z11^T (upper) * L21^T
-        sa.push_back(GemmDesc{c1, r2, c1, x.zld, x.ld, x.zld, x.z + p0 + (int64_t)p0 * x.zld,
-                              x.l + h + (int64_t)p0 * x.ld, x.z + p0 + (int64_t)h * x.zld});
-        // Z21 (r2 x c1) := -Z22 (lower) * Z12^T
-        sb.push_back(GemmDesc{r2, c1, r2, x.zld, x.zld, x.zld, x.z + h + (int64_t)h * x.zld,
-                              x.z + p0 + (int64_t)h * x.zld, x.z + h + (int64_t)p0 * x.zld});
+        if (tc) {
+          // Z12(i, j) = sum_k Z11(k, i) L21(j, k): A = Z11^T (K-major reads of Z11, upper), B = L21 (column form)
+          ta.push_back(TcGemm{x.z + p0 + (int64_t)p0 * x.zld, x.l + h + (int64_t)p0 * x.ld, x.z + p0 + (int64_t)h * x.zld,
+                              x.zld, x.ld, x.zld, c1, r2, c1, 1, 0, 2});
+          // Z21(i, j) = -sum_k Z22(i, k) Z12(j, k): A = Z22 (lower), B = Z12 (column form)
+          tb.push_back(TcGemm{x.z + h + (int64_t)h * x.zld, x.z + p0 + (int64_t)h * x.zld, x.z + h + (int64_t)p0 * x.zld,
+                              x.zld, x.zld, x.zld, r2, c1, r2, 0, 0, 1});
+        } else {
+          // Z12 (c1 x r2) := Z11^T (upper) * L21^T
+          sa.push_back(GemmDesc{c1, r2, c1, x.zld, x.ld, x.zld, x.z + p0 + (int64_t)p0 * x.zld,
+                                x.l + h + (int64_t)p0 * x.ld, x.z + p0 + (int64_t)h * x.zld});
+          // Z21 (r2 x c1) := -Z22 (lower) * Z12^T
+          sb.push_back(GemmDesc{r2, c1, r2, x.zld, x.zld, x.zld, x.z + h + (int64_t)h * x.zld,
+                                x.z + p0 + (int64_t)h * x.zld, x.z + h + (int64_t)p0 * x.zld});
+        }
         if (flops) *flops += (double)c1 * c1 * r2 + (double)r2 * r2 * c1;
+      }
+    }
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) {
+        if (ta.empty()) continue;
+        tc_gemm(st, ring, ta, 1.f, 0.f, zbase, lbase, zbase, status);
+        tc_gemm(st, ring, tb, -1.f, 0.f, zbase, zbase, zbase, status);
+        continue;
       }
     }
     if (sa.empty()) continue;
@@ -877,7 +898,9 @@ void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriD
   }
 }
 
-template void trtri_from_blocks<float>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const float*, float*, double*);
-template void trtri_from_blocks<double>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const double*, double*, double*);
+template void trtri_from_blocks<float>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const float*, float*, double*,
+                                        int*);
+template void trtri_from_blocks<double>(cudaStream_t, DescRing&, const std::vector<TrtriDesc>&, const double*, double*,
+                                         double*, int*);
 
 }  // namespace amb

@@ -223,15 +223,16 @@ void Engine<T>::factor_level(LevelData<T>& L) {
     for (int s = 0; s < ns; ++s) {
       if (L.ni[s] > 0) t.push_back(TrtriDesc{L.pM.off[s], L.pLI.off[s], L.nn[s], L.ni[s], L.ni[s], 0});
     }
-    trtri_from_blocks<T>(st, ring, t, dptr<T>(L.M), dptr<T>(L.LinvI), &ft_);
+    trtri_from_blocks<T>(st, ring, t, dptr<T>(L.M), dptr<T>(L.LinvI), &ft_, dptr<int>(status));
     t.clear();
     for (int s = 0; s < ns; ++s) {
       if (L.nd[s] > 0)
         t.push_back(TrtriDesc{L.pM.off[s] + L.ni[s] + (int64_t)L.ni[s] * L.nn[s], L.pLD.off[s], L.nn[s], L.nd[s],
                               L.nd[s], 0});
     }
-    trtri_from_blocks<T>(st, ring, t, dptr<T>(L.M), dptr<T>(L.LinvD), &ft_);
+    trtri_from_blocks<T>(st, ring, t, dptr<T>(L.M), dptr<T>(L.LinvD), &ft_, dptr<int>(status));
   }
+  check_status("explicit triangular inverses", AMB_ETIMEOUT);
   tm.fam_flops[AMB_FAM_TRTRI] += ft_;
   L.trtri_flops += ft_;
   AMB_CUDA(cudaStreamSynchronize(st));

@@ -1,14 +1,20 @@
-// Trailing update of the blocked Cholesky (Sec. 2: A_II = L L^T and, through
-// the same elimination, S = K_GG - X^T X) on the 5th-generation tensor cores:
+// Dense products of the FP32 form on the 5th-generation tensor cores:
 //
-//   C(lower) = beta C + alpha P P^T,   P = rem x K, C = rem x rem,
+// - the trailing update of the blocked Cholesky (Sec. 2: A_II = L L^T and,
+//   through the same elimination, S = K_GG - X^T X),
+//     C(lower) = beta C + alpha P P^T,   P = rem x K (K <= 256);
+// - general products C = beta C + alpha A B^T with an optionally triangular
+//   A (the merges of the explicit triangular inverses), K taken in chunks of
+//   256 whose partial products are added into C in FP32.
 //
-// in FP32 accuracy from three TF32 products (P = P_h + P_l, both TF32-exact:
-// P P^T ~ P_h P_h^T + P_h P_l^T + P_l P_h^T, the P_l P_l^T term is below FP32
-// rounding).  A split pass writes P_h and P_l row-major (K contiguous, the
-// K-major operand layout of tcgen05.mma kind::tf32) into a workspace slab,
-// each substructure's rows padded to a multiple of 128 and K to a multiple
-// of 32, with zeros.
+// Both in FP32 accuracy from three TF32 products (P = P_h + P_l, both
+// TF32-exact: P P^T ~ P_h P_h^T + P_h P_l^T + P_l P_h^T, the P_l P_l^T term
+// is below FP32 rounding).  A split pass writes the operands' high and low
+// parts row-major (K contiguous, the K-major operand layout of tcgen05.mma
+// kind::tf32) into a workspace slab, rows padded to a multiple of 128 and K
+// to a multiple of 32 with zeros (entries outside a triangular operand's
+// triangle are zero too); a row tile of a triangular A runs only over the
+// K blocks that hold its entries.
 //
 // The tile kernel is persistent (one CTA per SM, 128 x 128 output tiles
 // taken round-robin) and warp-specialized: warp 0 loads 128 x 32 operand
@@ -16,7 +22,10 @@
 // owns the TMEM accumulators and issues the MMAs (one thread), and warps 2-5
 // drain the accumulators with tcgen05.ld (lane = row), hand TMEM back to the
 // MMA warp and then update C, so the next tile's MMAs overlap the epilogue's
-// C traffic.  Stage hand-offs use mbarriers: TMA completion (expect_tx),
+// C traffic.  The C update goes 64 columns at a time (all loads, then all
+// stores) with addresses formed by increments: with the 128 accumulator
+// registers live, per-column 64-bit offsets spilled and made the update
+// 2.3x slower.  Stage hand-offs use mbarriers: TMA completion (expect_tx),
 // MMA completion (tcgen05.commit), TMEM full / TMEM empty.
 //
 // Accuracy: the tensor cores' FP32 accumulation rounds toward zero, so a
@@ -79,18 +88,24 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// P (rem x K, column-major, ld) -> slab rows [row0, row0 + rpad), K-contiguous,
-// stride kp; entries outside rem x K are zero.  32 x 32 tiles through shared
-// memory (coalesced on both sides).
-__global__ void k_tc_split(const float* base, const TcSplitDesc* d, int kp, float* sh, float* sl) {
+// source block (rows x cols; column form: (r, k) at src + r + k*ld, K-major
+// form: src + k + r*ld) -> slab rows [row0, row0 + rpad), K-contiguous,
+// stride kp; entries outside rows x cols or outside the triangle are zero.
+// 32 x 32 tiles through shared memory (coalesced on both sides).
+__global__ void k_tc_split(const TcSplitDesc* d, int kp, float* sh, float* sl) {
   __shared__ float t[32][33];
   const TcSplitDesc x = d[blockIdx.z];
   const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
   if (r0 >= x.rpad || k0 >= kp) return;
   const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
   for (int q = ty; q < 32; q += 8) {
-    const int r = r0 + tx, k = k0 + q;
-    t[q][tx] = (r < x.rows && k < x.cols) ? base[x.src + r + (int64_t)k * x.ld] : 0.f;
+    // column form: lane = row; K-major form: lane = k (t is [k][r] either way)
+    const int r = x.kmajor ? r0 + q : r0 + tx, k = x.kmajor ? k0 + tx : k0 + q;
+    bool ok = r < x.rows && k < x.cols;
+    if (x.tri == 1 && k - r > x.diag) ok = false;
+    if (x.tri == 2 && k - r < x.diag) ok = false;
+    const float v = ok ? (x.kmajor ? x.src[k + (int64_t)r * x.ld] : x.src[r + (int64_t)k * x.ld]) : 0.f;
+    if (x.kmajor) t[tx][q] = v; else t[q][tx] = v;
   }
   __syncthreads();
   for (int q = ty; q < 32; q += 8) {
@@ -148,6 +163,17 @@ __device__ __forceinline__ void tile_coords(const TcTileArgs& g, int tile, TcDes
   }
 }
 
+// K blocks [kb, ke) of a tile: a triangular A has no entries in part of the
+// chunk for a given row block
+__device__ __forceinline__ void tile_krange(const TcDesc& d, int ti, int& kb, int& ke) {
+  kb = 0;
+  ke = d.k / kTK;
+  const int ib = d.ioff + ti * kTM;   // global row - chunk k of the tile's first row
+  if (d.tri == 1) ke = min(ke, max(0, (ib + kTM + kTK - 1) / kTK));
+  if (d.tri == 2) kb = max(kb, ib / kTK);
+  if (kb > ke) kb = ke;
+}
+
 __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUtensorMap map_h,
                                                    const __grid_constant__ CUtensorMap map_l, TcTileArgs g) {
   extern __shared__ uint8_t smem_raw[];
@@ -189,8 +215,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
         int ti, tj;
         tile_coords(g, tile, d, ti, tj);
         const int ya = (int)(d.arow + (int64_t)ti * kTM), yb = (int)(d.brow + (int64_t)tj * kTN);
-        const int nk = d.k / kTK;
-        for (int kt = 0; kt < nk; ++kt, ++it) {
+        int kb, ke;
+        tile_krange(d, ti, kb, ke);
+        for (int kt = kb; kt < ke; ++kt, ++it) {
           const int s = it % kStages;
           if (!role_wait(smem_u32(&empty[s]), ((it / kStages) & 1) ^ 1, &abort_sh, g.status)) break;
           const uint32_t sb = smem_u32(smem + s * kStageBytes), fb = smem_u32(&full[s]);
@@ -210,10 +237,11 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
         TcDesc d;
         int ti, tj;
         tile_coords(g, tile, d, ti, tj);
-        const int nk = d.k / kTK;
+        int kb, ke;
+        tile_krange(d, ti, kb, ke);
         if (!role_wait(smem_u32(&tempty), (tl & 1) ^ 1, &abort_sh, g.status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int kt = 0; kt < nk; ++kt, ++it) {
+        for (int kt = kb; kt < ke; ++kt, ++it) {
           const int s = it % kStages;
           if (!role_wait(smem_u32(&full[s]), (it / kStages) & 1, &abort_sh, g.status)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -223,7 +251,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
             const uint32_t ko = kk * 32;   // K = 8 per MMA: 32 bytes along the swizzled row
             const uint64_t dah = smem_desc_sw128(sb + ko), dal = smem_desc_sw128(sb + kTileBytes + ko);
             const uint64_t dbh = smem_desc_sw128(sb + 2 * kTileBytes + ko), dbl = smem_desc_sw128(sb + 3 * kTileBytes + ko);
-            const int step = kt * (kTK / 8) + kk;
+            const int step = (kt - kb) * (kTK / 8) + kk;
             mma_tf32(tacc + (uint32_t)((step % 3) * kTN), dah, dbh, step >= 3 ? 1u : 0u);
             mma_tf32(tacc + (uint32_t)(3 * kTN), dah, dbl, step >= 1 ? 1u : 0u);
             mma_tf32(tacc + (uint32_t)(3 * kTN), dal, dbh, 1u);
@@ -245,7 +273,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
       TcDesc d;
       int ti, tj;
       tile_coords(g, tile, d, ti, tj);
-      const int nsteps = (d.k / kTK) * (kTK / 8);
+      int kb, ke;
+      tile_krange(d, ti, kb, ke);
+      const int nsteps = (ke - kb) * (kTK / 8);
       if (!role_wait(smem_u32(&tfull), tl & 1, &abort_sh, g.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       float acc[kTN];
@@ -267,8 +297,8 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
         // accumulators not yet written (fewer than three K = 8 steps) hold no data
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          float v = __uint_as_float(r[3][q]);
-          if (nsteps > 0) v += __uint_as_float(r[0][q]);
+          float v = 0.f;
+          if (nsteps > 0) v = __uint_as_float(r[3][q]) + __uint_as_float(r[0][q]);
           if (nsteps > 1) v += __uint_as_float(r[1][q]);
           if (nsteps > 2) v += __uint_as_float(r[2][q]);
           acc[h * 16 + q] = v;
@@ -279,24 +309,28 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty)) : "memory");
       const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
+      const float beta = d.first ? g.beta : 1.f;
       if (i < d.m) {
-        float* row = g.c + d.c + i;
-        // 64 columns at a time: all loads first, then the stores
+        // 64 columns at a time: the loads first, then the stores; addresses
+        // by increments so that no per-column 64-bit offsets stay live
+        const int64_t ldc = d.ldc;
+        const int jlast = min(d.n, d.lower ? i + 1 : d.n) - 1;   // last column this row updates
+        float* const p0 = g.c + d.c + i + (int64_t)tj * kTN * ldc;
 #pragma unroll
         for (int cb = 0; cb < kTN / 64; ++cb) {
           const int j0 = tj * kTN + cb * 64;
           float cv[64];
+          const float* p = p0 + (int64_t)cb * 64 * ldc;
 #pragma unroll
           for (int q = 0; q < 64; ++q) {
-            const int j = j0 + q;
-            const bool w = j < d.n && !(d.lower && j > i);
-            cv[q] = (w && g.beta != 0.f) ? __ldcg(row + (int64_t)j * d.ldc) : 0.f;
+            cv[q] = (j0 + q <= jlast && beta != 0.f) ? __ldcg(p) : 0.f;
+            p += ldc;
           }
+          float* o = p0 + (int64_t)cb * 64 * ldc;
 #pragma unroll
           for (int q = 0; q < 64; ++q) {
-            const int j = j0 + q;
-            if (j >= d.n || (d.lower && j > i)) continue;
-            row[(int64_t)j * d.ldc] = fmaf(g.beta, cv[q], g.alpha * acc[cb * 64 + q]);
+            if (j0 + q <= jlast) *o = fmaf(beta, cv[q], g.alpha * acc[cb * 64 + q]);
+            o += ldc;
           }
         }
       }
@@ -357,40 +391,26 @@ int tc_tile_count(const TcDesc& x) {
   return tm * ((x.n + kTN - 1) / kTN);
 }
 
-void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, float alpha, float beta,
-                   float* base, int* status) {
-  if (d.empty()) return;
+namespace {
+
+// one split launch over sp, then one persistent tile launch over td
+void run_tiles(cudaStream_t st, DescRing& ring, const std::vector<TcSplitDesc>& sp, const std::vector<TcDesc>& td,
+               std::vector<int> prefix, int64_t rows, int maxr, int64_t tiles, float alpha, float beta, float* cbase,
+               int* status) {
   static thread_local bool attr = false;
   if (!attr) {
     AMB_CUDA(cudaFuncSetAttribute(k_tc_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     attr = true;
   }
   constexpr int kp = kTcKMax;
-  std::vector<TcSplitDesc> sp;
-  std::vector<TcDesc> td;
-  std::vector<int> prefix;
-  int64_t rows = 0;
-  int maxr = 0;
-  int64_t tiles = 0;
-  for (const auto& x : d) {
-    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
-    if (x.rem <= 0 || x.k <= 0) continue;
-    const int rpad = (x.rem + kTM - 1) / kTM * kTM;
-    sp.push_back(TcSplitDesc{x.p, rows, x.ld, x.rem, x.k, rpad});
-    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0};
-    prefix.push_back((int)tiles);
-    tiles += tc_tile_count(t);
-    td.push_back(t);
-    rows += rpad;
-    maxr = std::max(maxr, rpad);
-  }
-  if (td.empty()) return;
-  AMB_CHECK(tiles < (1LL << 31) && sp.size() < 65536, AMB_EINVAL, "tensor-core batch too large");
+  AMB_CHECK(tiles < (1LL << 31) && rows < (1LL << 31) && sp.size() < 65536, AMB_EINVAL,
+            "tensor-core batch too large");
   prefix.push_back((int)tiles);
+  std::vector<TcSplitDesc> spr(sp);
   float* sh = tc_slab((size_t)rows * kp);
   float* sl = sh + (size_t)rows * kp;
-  const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(sp.data(), sp.size() * sizeof(TcSplitDesc), st));
-  k_tc_split<<<dim3((unsigned)(maxr / 32), kp / 32, (unsigned)sp.size()), dim3(32, 8), 0, st>>>(base, dsp, kp, sh, sl);
+  const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(spr.data(), spr.size() * sizeof(TcSplitDesc), st));
+  k_tc_split<<<dim3((unsigned)(maxr / 32), kp / 32, (unsigned)spr.size()), dim3(32, 8), 0, st>>>(dsp, kp, sh, sl);
   AMB_LAUNCHED();
   std::vector<char> blob(td.size() * sizeof(TcDesc) + prefix.size() * sizeof(int));
   memcpy(blob.data(), td.data(), td.size() * sizeof(TcDesc));
@@ -407,18 +427,113 @@ void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d
   g.al = sl;
   g.bh = sh;
   g.bl = sl;
-  g.c = base;
+  g.c = cbase;
   g.status = status;
   static thread_local int nsm = 0;
   if (nsm == 0) {
-    int dev = 0;
-    AMB_CUDA(cudaGetDevice(&dev));
-    AMB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    int devid = 0;
+    AMB_CUDA(cudaGetDevice(&devid));
+    AMB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, devid));
   }
   const CUtensorMap mh = slab_map(sh, rows, kp), ml = slab_map(sl, rows, kp);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
   k_tc_syrk<<<grid, 192, kSmemBytes, st>>>(mh, ml, g);
   AMB_LAUNCHED();
+}
+
+int pad_rows(int r) { return (r + kTM - 1) / kTM * kTM; }
+
+}  // namespace
+
+void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, float alpha, float beta,
+                   float* base, int* status) {
+  if (d.empty()) return;
+  constexpr int kp = kTcKMax;
+  std::vector<TcSplitDesc> sp;
+  std::vector<TcDesc> td;
+  std::vector<int> prefix;
+  int64_t rows = 0, tiles = 0;
+  int maxr = 0;
+  for (const auto& x : d) {
+    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
+    if (x.rem <= 0 || x.k <= 0) continue;
+    const int rpad = pad_rows(x.rem);
+    sp.push_back(TcSplitDesc{base + x.p, rows, x.ld, x.rem, x.k, rpad, 0, 0, 0, 0});
+    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0, 0, 1};
+    prefix.push_back((int)tiles);
+    tiles += tc_tile_count(t);
+    td.push_back(t);
+    rows += rpad;
+    maxr = std::max(maxr, rpad);
+  }
+  if (td.empty()) return;
+  run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, base, status);
+}
+
+void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,
+             const float* abase, const float* bbase, float* cbase, int* status) {
+  constexpr int kp = kTcKMax;
+  int kmax = 0;
+  for (const auto& x : d) {
+    AMB_CHECK(x.m >= 0 && x.n >= 0 && x.k >= 0 && x.a_tri >= 0 && x.a_tri <= 2, AMB_EINVAL, "bad tensor-core product");
+    // rows of an upper-triangular A beyond K would never be written
+    AMB_CHECK(x.a_tri != 2 || x.m <= x.k, AMB_EINVAL, "upper-triangular tensor-core operand with m > k");
+    if (x.m > 0 && x.n > 0) kmax = std::max(kmax, x.k);
+  }
+  for (int k0 = 0; k0 < kmax || (k0 == 0 && kmax == 0); k0 += kp) {
+    std::vector<TcSplitDesc> sp;
+    std::vector<TcDesc> td;
+    std::vector<int> prefix;
+    int64_t rows = 0, tiles = 0;
+    int maxr = 0;
+    for (const auto& x : d) {
+      if (x.m <= 0 || x.n <= 0) continue;
+      if (x.k <= 0) {
+        // an empty sum: C = beta C, as one chunk with no K steps
+        if (k0 > 0) continue;
+      } else if (k0 >= x.k) {
+        continue;
+      }
+      const int k1 = std::min(x.k, k0 + kp), kc = std::max(0, k1 - k0);
+      // row ranges of A with entries in [k0, k1), and whether beta applies
+      // (the chunk is the first that reaches those rows)
+      int rr[2][3];
+      int nr = 0;
+      if (x.a_tri == 2) {
+        const int hi = std::min(x.m, std::max(k1, 1));
+        if (k0 > 0 && std::min(k0, x.m) > 0) rr[nr][0] = 0, rr[nr][1] = std::min(k0, x.m), rr[nr][2] = 0, ++nr;
+        if (hi > k0) rr[nr][0] = k0, rr[nr][1] = hi, rr[nr][2] = 1, ++nr;
+      } else if (x.a_tri == 1) {
+        if (k0 == 0) rr[nr][0] = 0, rr[nr][1] = x.m, rr[nr][2] = 1, ++nr;
+        else if (k0 < x.m) rr[nr][0] = k0, rr[nr][1] = x.m, rr[nr][2] = 0, ++nr;
+      } else {
+        rr[nr][0] = 0, rr[nr][1] = x.m, rr[nr][2] = k0 == 0, ++nr;
+      }
+      if (nr == 0) continue;
+      // B rows (all n) for this chunk
+      const int npad = pad_rows(x.n);
+      const int64_t brow = rows;
+      sp.push_back(TcSplitDesc{bbase + x.b + (x.b_kmajor ? (int64_t)k0 : (int64_t)k0 * x.ldb), brow, x.ldb, x.n, kc,
+                               npad, x.b_kmajor, 0, 0, 0});
+      rows += npad;
+      maxr = std::max(maxr, npad);
+      for (int q = 0; q < nr; ++q) {
+        const int r0 = rr[q][0], r1 = rr[q][1];
+        const int mpad = pad_rows(r1 - r0);
+        const int64_t aoff = x.a_kmajor ? (int64_t)k0 + (int64_t)r0 * x.lda : (int64_t)r0 + (int64_t)k0 * x.lda;
+        sp.push_back(TcSplitDesc{abase + x.a + aoff, rows, x.lda, r1 - r0, kc, mpad, x.a_kmajor, x.a_tri, r0 - k0, 0});
+        TcDesc t{x.c + r0, rows, brow, r1 - r0, x.n, (kc + kTK - 1) / kTK * kTK, x.ldc, 0, x.a_tri, r0 - k0, rr[q][2]};
+        prefix.push_back((int)tiles);
+        tiles += tc_tile_count(t);
+        td.push_back(t);
+        rows += mpad;
+        maxr = std::max(maxr, mpad);
+      }
+    }
+    if (td.empty()) break;
+    run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, cbase, status);
+    if (kmax == 0) break;
+  }
 }
 
 }  // namespace amb

@@ -16,16 +16,32 @@ struct TcSyrk {
   int32_t ld, rem, k, pad;
 };
 
-// split pass: source block (column-major) -> slab rows [row0, row0 + rpad)
-struct TcSplitDesc {
-  int64_t src, row0;
-  int32_t ld, rows, cols, rpad;
+// One product C = beta C + alpha A B^T (C m x n column-major, ldc).  A(i, k)
+// sits at a + i + k*lda (column form) or a + k + i*lda (K-major form), B(j, k)
+// likewise.  a_tri: 0 dense, 1 lower (A(i, k) = 0 for k > i), 2 upper
+// (A(i, k) = 0 for k < i); the entries outside the triangle are not read.
+struct TcGemm {
+  int64_t a, b, c;
+  int32_t lda, ldb, ldc, m, n, k;
+  int32_t a_kmajor, b_kmajor, a_tri;
 };
 
-// one product C = beta C + alpha A B^T with A rows at slab row arow, B rows at brow
+// split pass: a rows x cols source block -> slab rows [row0, row0 + rpad),
+// entries outside it (and outside the triangle) zero
+struct TcSplitDesc {
+  const float* src;
+  int64_t row0;
+  int32_t ld, rows, cols, rpad;
+  int32_t kmajor, tri, diag, pad;             // tri as in TcGemm; diag = global row - global k at (0, 0)
+};
+
+// one tile job list entry: C rows at c (element offset) from A slab rows arow,
+// B slab rows brow; lower: only the lower triangle of a square C.  tri/ioff
+// narrow each row tile's K range (ioff = global row of row 0 - global k of
+// slab column 0); first: beta applies (else the chunk accumulates onto C).
 struct TcDesc {
   int64_t c, arow, brow;
-  int32_t m, n, k, ldc, lower, pad;
+  int32_t m, n, k, ldc, lower, tri, ioff, first;
 };
 
 struct TcTileArgs {
@@ -43,5 +59,10 @@ int tc_tile_count(const TcDesc& x);
 // C(lower) = beta C + alpha P P^T for every entry of d (FP32 data in base).
 void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, float alpha, float beta,
                    float* base, int* status);
+
+// C = beta C + alpha A B^T for every entry of d (A from abase, B from bbase,
+// C in cbase), K in chunks of kTcKMax accumulated in FP32 through C.
+void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,
+             const float* abase, const float* bbase, float* cbase, int* status);
 
 }  // namespace amb
