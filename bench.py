@@ -31,9 +31,27 @@ import amb_inputs as ai  # noqa: E402
 
 METRIC = "adaptive-BDDC setup+solve s to 1e-8 rel. residual; Schur-apply % of roofline"
 WORKLOAD = "elasticity48_4x4x4_lognormal"
-# DRAM bytes per algorithmic flop of the tensor-core trailing update, from the ncu capture summarised in
-# profiles/k_tc_syrk_elasticity48_block2x2x2.md (None when the kernel has changed since)
-TC_TRAFFIC_PER_FLOP = None
+# DRAM bytes per 128 x 128 output tile of the tensor-core trailing update, from the ncu capture summarised in
+# profiles/k_tc_syrk_elasticity48_block2x2x2.md (one launch: 1,036,088,832 bytes over 7240 tiles; None when
+# the kernel has changed since)
+TC_TRAFFIC_PER_TILE = 1036088832 / 7240
+TC_OUTER, TC_TILE = 256, 128
+
+
+def tc_tiles(n_i, n_g, n_d):
+    """Output tiles of all trailing updates of one set-up: the interior factorization (columns 0..n_I of the
+    (n_I + n_G)-square matrix) and the corner-constrained Neumann one (columns n_I..n_I + n_D), one update per
+    256-column outer block, lower-triangular tiles of the remaining rows."""
+    t = 0
+    for ni, ng, nd in zip(n_i.astype(int), n_g.astype(int), n_d.astype(int)):
+        n = ni + ng
+        for c0, c1 in ((0, ni), (ni, ni + nd)):
+            for j1 in range(c0 + TC_OUTER, c1 + TC_OUTER, TC_OUTER):
+                rem = n - min(j1, c1)
+                tm = -(-rem // TC_TILE)
+                if rem > 0:
+                    t += tm * (tm + 1) // 2
+    return t
 
 
 def _peaks():
@@ -276,8 +294,13 @@ def main():
         ach = tc["flops"] / (tc["ms"] * 1e-3) / 1e12
         roofline = {"kernel": "k_tc_syrk (+ k_tc_split): Cholesky trailing update C -= P P^T, 3xTF32 on tcgen05",
                     "bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
-                    "tensor_pipe_frac": 3.0 * ach / tf32_peak, "traffic": TC_TRAFFIC_PER_FLOP * tc["flops"] / tc["launches"]
-                    if TC_TRAFFIC_PER_FLOP and tc["launches"] else None,
+                    "tensor_pipe_frac": 3.0 * ach / tf32_peak,
+                    "traffic": TC_TRAFFIC_PER_TILE * tc_tiles(n_i, n_g, n_d) / (tc["launches"] // 2)
+                    if TC_TRAFFIC_PER_TILE and tc["launches"] >= 2 else None,
+                    "traffic_note": "k_tc_syrk DRAM bytes per launch (each update = one k_tc_split + one k_tc_syrk "
+                                    "launch): bytes per 128x128 tile from one ncu capture (48^3 corner block, 7240 "
+                                    "tiles) x this step's tiles / updates; the split pass is not included",
+                    "algorithmic_bytes_per_tile": 2 * 4 * TC_TILE * TC_TILE,
                     "launches": tc["launches"], "ms": tc["ms"],
                     "peak_source": f"{src} bf16 dense burst x nominal TF32/BF16 ratio (of {src})",
                     "units": "flops = 2 per lower-triangle multiply-add; tensor_pipe_frac counts the three TF32 "

@@ -375,9 +375,11 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   psi_rhs<T>(st, dptr<T>(Z2), dptr<int64_t>(dz), dptr<T>(L.S), dptr<int64_t>(L.par), ns, imax(L.nd), imax(L.nc));
   if constexpr (!std::is_same<T, double>::value)
     convert<double, T>(st, dptr<double>(Z2d), dptr<T>(Z2), pZ.total);
+  // only the corner columns of R are nonzero: Z3 = [L_D^{-1} R_c | 0]
+  AMB_CUDA(cudaMemsetAsync(Z3d.p, 0, pZ.total * sizeof(double), st));
   d.clear();
   for (int s = 0; s < ns; ++s)
-    d.push_back(GemmDesc{L.nd[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
+    d.push_back(GemmDesc{L.nd[s], L.ncrn[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.nd[s], 1), L.pLD.off[s], pZ.off[s], pZ.off[s]});
   gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER, 1.0, 0.0, dptr<T>(L.LinvD), z2d, dptr<double>(Z3d));
   // W1 = Yd^T Z3 - [0 | I]

@@ -52,59 +52,54 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
-// Cyclic Jacobi eigen-decomposition of a symmetric n x n matrix in shared
-// memory (column-major, leading dimension ld >= n + (n & 1)).  Each round
-// rotates the disjoint index pairs of a round-robin ordering at once, and the
-// two-sided update is applied block-wise: B <- R_k^T B R_l on the 2 x 2 block
-// of index pairs (k, l), k <= l, mirrored to (l, k), with V <- V R in the
-// same pass (one barrier per round; only the upper blocks are computed).  For
-// odd n the extra index n is a zero row and column that is never rotated.
-// On exit A holds the eigenvalues on its diagonal, V the eigenvectors.
-__device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, double* cs, double* sn, int* P,
-                           int* Q) {
+// Cyclic Jacobi sweeps on a symmetric n x n matrix in shared memory
+// (column-major, leading dimension ld >= n + (n & 1)), accumulating the
+// rotations into V (V *= R).  Each round rotates the disjoint index pairs of
+// a round-robin ordering at once, and the two-sided update is applied
+// block-wise: B <- R_k^T B R_l on the 2 x 2 block of index pairs (k, l),
+// k <= l, mirrored to (l, k), with V <- V R in the same pass (one barrier per
+// round; only the upper blocks are computed).  For odd n the extra index n is
+// a zero row and column that is never rotated.  Stops when the off-diagonal
+// Frobenius norm squared is at most tol times the total, or after maxs sweeps.
+template <typename F>
+__device__ void jacobi_sweeps(F* A, F* V, int n, int ld, double* red, double* cs, double* sn, int* P, int* Q,
+                              double tol, int maxs) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ne = n + (n & 1), half = ne / 2;
-  for (int idx = tid; idx < ne * ne; idx += nt) {
-    int r = idx % ne, c = idx / ne;
-    V[r + c * ld] = (r == c) ? 1.0 : 0.0;
-    if (r == n || c == n) A[r + c * ld] = 0.0;
-  }
-  __syncthreads();
-  if (n <= 1) return;
   const int nblk = half * (half + 1) / 2;
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  // rotations below this relative size are skipped (FP64: far below rounding)
+  const double skip = sizeof(F) == 8 ? 1e-18 : 1e-9;
+  for (int sweep = 0; sweep < maxs; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = tid; idx < n * n; idx += nt) {
       int r = idx % n, c = idx / n;
-      double a = A[r + c * ld];
+      double a = (double)A[r + c * ld];
       tot += a * a;
       if (r != c) off += a * a;
     }
     off = block_sum(off, red);
     tot = block_sum(tot, red);
-    // off-diagonal Frobenius norm below 1e-13 of the total: converged (the
-    // FP64 rounding floor is near 1e-16, so a tighter test may never pass)
-    if (off <= 1e-26 * tot || tot == 0.0) break;
+    if (off <= tol * tot || tot == 0.0) break;
     for (int round = 0; round < ne - 1; ++round) {
       for (int k = tid; k < half; k += nt) {
         int a = (k == 0) ? 0 : 1 + ((k - 1 + round) % (ne - 1));
         int b = 1 + ((ne - 2 - k + round) % (ne - 1));
         int p = a < b ? a : b, q = a < b ? b : a;
-        double c = 1.0, s = 0.0;
+        F c = F(1), s = F(0);
         if (q < n) {
-          double apq = A[p + q * ld];
-          double app = A[p + p * ld], aqq = A[q + q * ld];
-          if (fabs(apq) > 1e-300 && fabs(apq) > 1e-18 * sqrt(fabs(app * aqq))) {
-            double th = (aqq - app) / (2.0 * apq);
-            double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            c = 1.0 / sqrt(t * t + 1.0);
+          F apq = A[p + q * ld];
+          F app = A[p + p * ld], aqq = A[q + q * ld];
+          if (fabs((double)apq) > 1e-300 && fabs((double)apq) > skip * sqrt(fabs((double)app * (double)aqq))) {
+            F th = (aqq - app) / (F(2) * apq);
+            F t = (th >= F(0) ? F(1) : F(-1)) / (F(fabs((double)th)) + F(sqrt((double)th * (double)th + 1.0)));
+            c = F(1) / F(sqrt((double)t * (double)t + 1.0));
             s = t * c;
           }
         }
         P[k] = p;
         Q[k] = q;
-        cs[k] = c;
-        sn[k] = s;
+        cs[k] = (double)c;
+        sn[k] = (double)s;
       }
       __syncthreads();
       for (int idx = tid; idx < nblk + n * half; idx += nt) {
@@ -114,15 +109,15 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, dou
           while (l * (l + 1) / 2 > idx) --l;
           while ((l + 1) * (l + 2) / 2 <= idx) ++l;
           const int k = idx - l * (l + 1) / 2;
-          const double sk = sn[k], sl = sn[l];
-          if (sk == 0.0 && sl == 0.0) continue;
-          const double ck = cs[k], cl = cs[l];
+          const F sk = (F)sn[k], sl = (F)sn[l];
+          if (sk == F(0) && sl == F(0)) continue;
+          const F ck = (F)cs[k], cl = (F)cs[l];
           const int pk = P[k], qk = Q[k], pl = P[l], ql = Q[l];
-          const double b00 = A[pk + pl * ld], b01 = A[pk + ql * ld], b10 = A[qk + pl * ld], b11 = A[qk + ql * ld];
-          const double t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
-          const double t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
-          const double n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
-          const double n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
+          const F b00 = A[pk + pl * ld], b01 = A[pk + ql * ld], b10 = A[qk + pl * ld], b11 = A[qk + ql * ld];
+          const F t00 = cl * b00 - sl * b01, t01 = sl * b00 + cl * b01;
+          const F t10 = cl * b10 - sl * b11, t11 = sl * b10 + cl * b11;
+          const F n00 = ck * t00 - sk * t10, n01 = ck * t01 - sk * t11;
+          const F n10 = sk * t00 + ck * t10, n11 = sk * t01 + ck * t11;
           if (k == l) {
             A[pk + pk * ld] = n00;
             A[qk + qk * ld] = n11;
@@ -140,11 +135,11 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, dou
           }
         } else {
           const int v = idx - nblk, l = v / n, i = v % n;
-          const double sl = sn[l];
-          if (sl == 0.0) continue;
-          const double cl = cs[l];
+          const F sl = (F)sn[l];
+          if (sl == F(0)) continue;
+          const F cl = (F)cs[l];
           const int pl = P[l], ql = Q[l];
-          const double vp = V[i + pl * ld], vq = V[i + ql * ld];
+          const F vp = V[i + pl * ld], vq = V[i + ql * ld];
           V[i + pl * ld] = cl * vp - sl * vq;
           V[i + ql * ld] = sl * vp + cl * vq;
         }
@@ -152,6 +147,101 @@ __device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, dou
       __syncthreads();
     }
   }
+}
+
+// D = X^T Y (transx) or X Y, n x n, all in shared memory with leading dimension ld
+__device__ void small_gemm(double* D, const double* X, const double* Y, int n, int ld, bool transx) {
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    double s = 0.0;
+    if (transx)
+      for (int k = 0; k < n; ++k) s = fma(X[k + r * ld], Y[k + c * ld], s);
+    else
+      for (int k = 0; k < n; ++k) s = fma(X[r + k * ld], Y[k + c * ld], s);
+    D[r + c * ld] = s;
+  }
+  __syncthreads();
+}
+
+// Eigen-decomposition of a symmetric n x n matrix in shared memory: on exit A
+// holds the eigenvalues on its diagonal, V the eigenvectors (FP64 accuracy).
+// FP64 runs at 1/64 of the FP32 rate on this GPU, so with scratch space
+// (T, W: ld x ld doubles each; may be null) the sweeps start in FP32 on a
+// copy of A (to a relative off-diagonal norm of 1e-5); the FP32 rotations are
+// then made orthonormal in FP64 (two Newton-Schulz steps V <- V (3I - V^T V)/2),
+// A is transformed to V^T A V in FP64, and FP64 sweeps finish from there
+// (quadratic convergence: two or three sweeps instead of about ten).  If the
+// FP32 rotations are not orthonormal to 1e-3 the FP32 part is discarded.
+__device__ void jacobi_eig(double* A, double* V, int n, int ld, double* red, double* cs, double* sn, int* P, int* Q,
+                           double* T = nullptr, double* W = nullptr) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ne = n + (n & 1);
+  for (int idx = tid; idx < ne * ne; idx += nt) {
+    int r = idx % ne, c = idx / ne;
+    V[r + c * ld] = (r == c) ? 1.0 : 0.0;
+    if (r == n || c == n) A[r + c * ld] = 0.0;
+  }
+  __syncthreads();
+  if (n <= 1) return;
+  if (T && W && n >= 8) {
+    float* A32 = reinterpret_cast<float*>(W);
+    float* V32 = A32 + ld * ld;
+    for (int idx = tid; idx < ne * ne; idx += nt) {
+      int r = idx % ne, c = idx / ne;
+      A32[r + c * ld] = (float)A[r + c * ld];
+      V32[r + c * ld] = (r == c) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    jacobi_sweeps<float>(A32, V32, n, ld, red, cs, sn, P, Q, 1e-10, 20);
+    for (int idx = tid; idx < n * n; idx += nt) {
+      int r = idx % n, c = idx / n;
+      V[r + c * ld] = (double)V32[r + c * ld];
+    }
+    __syncthreads();
+    // Newton-Schulz: T = V^T V, T <- (3I - T)/2, V <- V T (through W)
+    double dev = 0.0;
+    for (int step = 0; step < 2; ++step) {
+      small_gemm(T, V, V, n, ld, true);
+      double e = 0.0;
+      for (int idx = tid; idx < n * n; idx += nt) {
+        int r = idx % n, c = idx / n;
+        const double t = T[r + c * ld] - (r == c ? 1.0 : 0.0);
+        e = fmax(e, fabs(t));
+        T[r + c * ld] = (r == c ? 1.0 : 0.0) - 0.5 * t;
+      }
+      red[tid] = e;
+      __syncthreads();
+      for (int o = nt >> 1; o > 0; o >>= 1) {
+        if (tid < o) red[tid] = fmax(red[tid], red[tid + o]);
+        __syncthreads();
+      }
+      if (step == 0) dev = red[0];
+      __syncthreads();
+      if (!(dev <= 1e-3)) break;   // also catches NaN
+      small_gemm(W, V, T, n, ld, false);
+      for (int idx = tid; idx < n * n; idx += nt) V[(idx % n) + (idx / n) * ld] = W[(idx % n) + (idx / n) * ld];
+      __syncthreads();
+    }
+    if (dev <= 1e-3) {
+      // A <- V^T (A V), symmetrized
+      small_gemm(W, A, V, n, ld, false);
+      small_gemm(T, V, W, n, ld, true);
+      for (int idx = tid; idx < n * n; idx += nt) {
+        int r = idx % n, c = idx / n;
+        A[r + c * ld] = 0.5 * (T[r + c * ld] + T[c + r * ld]);
+      }
+      __syncthreads();
+    } else {
+      for (int idx = tid; idx < ne * ne; idx += nt) {
+        int r = idx % ne, c = idx / ne;
+        V[r + c * ld] = (r == c) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+    }
+  }
+  // off-diagonal Frobenius norm below 1e-13 of the total: converged (the
+  // FP64 rounding floor is near 1e-16, so a tighter test may never pass)
+  jacobi_sweeps<double>(A, V, n, ld, red, cs, sn, P, Q, 1e-26, 40);
 }
 
 // descending order of the diagonal of A (n <= kJacobiMax), by one thread
@@ -549,7 +639,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, c
     GB[r + c * ld] *= dsc[r] * dsc[c];
   }
   __syncthreads();
-  jacobi_eig(GB, V, w, ld, red, cs_, sn_, P_, Q_);
+  jacobi_eig(GB, V, w, ld, red, cs_, sn_, P_, Q_, Mr, Yr);   // Mr, Yr: scratch until Tm is formed
   sort_desc(GB, w, ld, ord);
   if (threadIdx.x == 0) {
     double smax = GB[ord[0] + ord[0] * ld];
@@ -590,7 +680,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, c
     }
   }
   __syncthreads();
-  jacobi_eig(Mr, GB, r, ld, red, cs_, sn_, P_, Q_);   // eigenvectors into GB (r x r, ld)
+  jacobi_eig(Mr, GB, r, ld, red, cs_, sn_, P_, Q_, GA, V);   // eigenvectors into GB (r x r, ld); GA, V: scratch
   sort_desc(Mr, r, ld, ord2);
   const int mm = min(m, r);
   // Cx(:, k) = D Tm y_k ; Cp = Cx with the X rows zeroed
