@@ -38,6 +38,18 @@ TC_TRAFFIC_PER_TILE = 1036088832 / 7240
 TC_OUTER, TC_TILE = 256, 128
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time per step: every rank runs one replica of the workload, so the job's time is
+    the maximum (all-reduce MAX over the process group; the identity on one rank)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def tc_tiles(n_i, n_g, n_d):
     """Output tiles of all trailing updates of one set-up: the interior factorization (columns 0..n_I of the
     (n_I + n_G)-square matrix) and the corner-constrained Neumann one (columns n_I..n_I + n_D), one update per
@@ -235,11 +247,7 @@ def main():
     e1.record()
     barrier()
     clk = clocks.stop(local)
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, "cuda")
     if args.profile:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": ms * 1e-3, "unit": "s", "profile_run": True,

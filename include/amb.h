@@ -154,7 +154,11 @@ typedef struct {
   double flops[AMB_FAM_N];      /* algorithmic flops issued (dense families) */
   double bytes[AMB_FAM_N];      /* algorithmic bytes (memory-bound families) */
   double phase_ms[8];           /* assembly, factor, eigen, constraints, coarse, solve, grad, total-setup */
-  int64_t kernels_launched;     /* all kernels launched by the library so far */
+  int64_t kernels_launched;     /* all kernels launched by the library so far (graph replays count
+                                   their kernels) */
+  int64_t tuned_shapes;         /* GEMM shape classes whose tile was chosen by timing (process-wide) */
+  int64_t tuning_runs;          /* GEMM runs spent timing candidate tiles (process-wide) */
+  int64_t graph_replays;        /* Algorithm-1 applications replayed from the context's CUDA graph */
 } amb_kernel_stats;
 
 /* Fill *o with the defaults: FP64, corners+edges, adaptive, 10 rows per

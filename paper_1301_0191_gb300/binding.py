@@ -72,7 +72,8 @@ class LevelSizes(C.Structure):
 
 class KernelStats(C.Structure):
     _fields_ = [("ms", C.c_double * FAM_N), ("launches", C.c_int64 * FAM_N), ("flops", C.c_double * FAM_N),
-                ("bytes", C.c_double * FAM_N), ("phase_ms", C.c_double * 8), ("kernels_launched", C.c_int64)]
+                ("bytes", C.c_double * FAM_N), ("phase_ms", C.c_double * 8), ("kernels_launched", C.c_int64),
+                ("tuned_shapes", C.c_int64), ("tuning_runs", C.c_int64), ("graph_replays", C.c_int64)]
 
 
 _lib = None
@@ -260,4 +261,5 @@ class Context:
                for i, name in enumerate(FAMILIES)}
         phases = dict(zip(("assembly", "factor", "eigen", "constraints", "coarse", "solve", "grad", "setup_total"),
                           list(s.phase_ms)))
-        return dict(families=fam, phase_ms=phases, kernels_launched=s.kernels_launched)
+        return dict(families=fam, phase_ms=phases, kernels_launched=s.kernels_launched,
+                    tuned_shapes=s.tuned_shapes, tuning_runs=s.tuning_runs, graph_replays=s.graph_replays)

@@ -437,6 +437,9 @@ int amb_stats(const amb_ctx* cc, amb_kernel_stats* st) {
   }
   for (int i = 0; i < 8; ++i) st->phase_ms[i] = c->tm.phase_ms[i];
   st->kernels_launched = c->launches_total;
+  st->tuned_shapes = (int64_t)gemm_tune_entries();
+  st->tuning_runs = gemm_tune_runs();
+  st->graph_replays = c->eng ? c->eng->graph_replays() : 0;
   return AMB_OK;
 }
 

@@ -99,10 +99,18 @@ class DescRing {
   ~DescRing() {
     if (host_) cudaFreeHost(host_);
   }
+  // a ring that must not wrap (the staging of a captured graph): allocated
+  // once, rewound to the start
+  void reset(size_t bytes) {
+    init(bytes);
+    pos_ = 0;
+    no_wrap_ = true;
+  }
   void* push(const void* src, size_t bytes, cudaStream_t st) {
     size_t need = (bytes + 255) & ~size_t(255);
     AMB_CHECK(need <= cap_, AMB_EINVAL, "descriptor batch larger than the staging ring");
     if (pos_ + need > cap_) {
+      AMB_CHECK(!no_wrap_, AMB_EINVAL, "graph descriptor staging ring too small");
       AMB_CUDA(cudaStreamSynchronize(st));
       pos_ = 0;
     }
@@ -118,7 +126,14 @@ class DescRing {
   void* host_ = nullptr;
   DevBuf dev_;
   size_t cap_ = 0, pos_ = 0;
+  bool no_wrap_ = false;
 };
+
+constexpr size_t kGraphRingBytes = size_t(16) << 20;   // descriptor staging of the preconditioner graph
+
+// tile autotuner bookkeeping (dense.cu): shape classes decided, runs spent timing
+size_t gemm_tune_entries();
+int64_t gemm_tune_runs();
 
 // One matrix product C = alpha op(A) op(B) + beta C of a batch; offsets are
 // element offsets from the launch's base pointers; matrices column-major.
@@ -136,6 +151,9 @@ enum GemmFlags : int {
   G_TRI_B_LOWER = 16,  // op(B)(l,j) = 0 for l < j
   G_TRI_B_UPPER = 32,  // op(B)(l,j) = 0 for l > j
   G_OUT_LOWER = 64,    // write only C(i,j) with i >= j
+  // the caller guarantees that running the product twice gives the same C
+  // (beta = 0, C overlaps neither A nor B): its tile shape may be autotuned
+  G_TUNE = 128,
 };
 
 // Batched product driver (dense.cu).  A may be stored in a narrower type

@@ -5,9 +5,12 @@
 // S = K_GG - X^T X with X = L^{-1} K_IG, and the corner-constrained Neumann
 // factor S_DD = L_D L_D^T) and every solve with those factors.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "common.h"
 #include "tc_gemm.h"
@@ -354,27 +357,137 @@ static void gemm_run(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc
   AMB_LAUNCHED();
 }
 
+// Tile autotuner.  A product flagged G_TUNE is run once with every tile
+// shape the first time its shape class is seen (types, flags, the widest
+// right-hand block exactly, and powers of two of the batch size, the
+// longest and the summed rows and the longest K, so that the shrinking
+// batches of an iteration reuse one entry); the fastest by CUDA events is
+// kept for the process.  Every shape accumulates each output over k in the
+// same order, so the choice does not change the result.  Products without
+// the flag, and products issued while the stream is being captured into a
+// graph, take the static rule (narrowest tile that covers the columns).
+namespace {
+
+enum TileChoice { TILE_SKINNY = 0, TILE_MEDIUM = 1, TILE_HALF = 2, TILE_WIDE = 3 };
+
+struct TuneKey {
+  int type, flags, ndesc, mmax, nmax, kmax;
+  int64_t msum, nsum, ksum;
+  bool operator==(const TuneKey& o) const {
+    return type == o.type && flags == o.flags && ndesc == o.ndesc && mmax == o.mmax && nmax == o.nmax &&
+           kmax == o.kmax && msum == o.msum && nsum == o.nsum && ksum == o.ksum;
+  }
+};
+struct TuneKeyHash {
+  size_t operator()(const TuneKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t v : {(int64_t)k.type, (int64_t)k.flags, (int64_t)k.ndesc, (int64_t)k.mmax, (int64_t)k.nmax,
+                      (int64_t)k.kmax, k.msum, k.nsum, k.ksum})
+      h = (h ^ (uint64_t)v) * 1099511628211ull;
+    return (size_t)h;
+  }
+};
+
+std::mutex g_tune_mu;
+std::unordered_map<TuneKey, int, TuneKeyHash> g_tune;
+std::atomic<int64_t> g_tune_runs{0};   // products run for tuning
+
+template <typename T, typename TA>
+void run_choice(int c, cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags, T alpha, T beta,
+                const TA* A, const T* B, T* C) {
+  switch (c) {
+    case TILE_SKINNY: gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
+    case TILE_MEDIUM: gemm_run<T, TA, GemmMedium<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
+    case TILE_HALF:
+      if constexpr (std::is_same<T, float>::value) {
+        gemm_run<T, TA, GemmHalfF>(st, ring, d, flags, alpha, beta, A, B, C);
+        break;
+      }
+      [[fallthrough]];
+    default: gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
+  }
+}
+
+}  // namespace
+
+int64_t gemm_tune_runs() { return g_tune_runs.load(); }
+size_t gemm_tune_entries() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tune.size();
+}
+
 template <typename T, typename TA>
 void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags,
                   T alpha, T beta, const TA* A, const T* B, T* C) {
-  int nmax = 0;
-  for (const auto& x : d) nmax = std::max(nmax, x.n);
+  int nmax = 0, mmax = 0, kmax = 0, nd = 0;
+  int64_t msum = 0, nsum = 0, ksum = 0;
+  for (const auto& x : d) {
+    if (x.m <= 0 || x.n <= 0) continue;
+    ++nd;
+    nmax = std::max(nmax, x.n);
+    mmax = std::max(mmax, x.m);
+    kmax = std::max(kmax, x.k);
+    msum += x.m;
+    nsum += x.n;
+    ksum += x.k;
+  }
+  if (nd == 0) return;
   const bool narrow_ok = !(flags & G_OUT_LOWER);
-  if (nmax <= 16 && narrow_ok) {
-    gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C);
+  // static rule
+  int choice = TILE_WIDE;
+  if (narrow_ok && nmax <= 16) choice = TILE_SKINNY;
+  else if (narrow_ok && nmax <= 32) choice = TILE_MEDIUM;
+  else if (std::is_same<T, float>::value && narrow_ok && nmax <= 64) choice = TILE_HALF;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  AMB_CUDA(cudaStreamIsCapturing(st, &cap));
+  if (!(flags & G_TUNE) || !narrow_ok || beta != T(0) || cap != cudaStreamCaptureStatusNone) {
+    run_choice<T, TA>(choice, st, ring, d, flags, alpha, beta, A, B, C);
     return;
   }
-  if (nmax <= 32 && narrow_ok) {
-    gemm_run<T, TA, GemmMedium<T>>(st, ring, d, flags, alpha, beta, A, B, C);
-    return;
-  }
-  if constexpr (std::is_same<T, float>::value) {
-    if (nmax <= 64 && narrow_ok) {
-      gemm_run<T, TA, GemmHalfF>(st, ring, d, flags, alpha, beta, A, B, C);
+  auto lg = [](int64_t v) {
+    int b = 0;
+    while (v > 1) v >>= 1, ++b;
+    return b;
+  };
+  const int type = (int)sizeof(T) * 16 + (int)sizeof(TA);
+  const TuneKey key{type, flags, lg(nd), lg(mmax), nmax, lg(kmax), lg(msum), 0, 0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      run_choice<T, TA>(it->second, st, ring, d, flags, alpha, beta, A, B, C);
       return;
     }
   }
-  gemm_run<T, TA, GemmTile<T>>(st, ring, d, flags, alpha, beta, A, B, C);
+  // candidates: every shape from the narrowest that covers the columns up
+  // to the widest (a narrower tile than the columns runs more column tiles)
+  std::vector<int> cand;
+  for (int c = TILE_SKINNY; c <= TILE_WIDE; ++c) {
+    if (c == TILE_HALF && !std::is_same<T, float>::value) continue;
+    cand.push_back(c);
+  }
+  cudaEvent_t e0, e1;
+  AMB_CUDA(cudaEventCreate(&e0));
+  AMB_CUDA(cudaEventCreate(&e1));
+  int best = choice;
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    AMB_CUDA(cudaEventRecord(e0, st));
+    run_choice<T, TA>(c, st, ring, d, flags, alpha, beta, A, B, C);
+    AMB_CUDA(cudaEventRecord(e1, st));
+    AMB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    ++g_tune_runs;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
 }
 
 template <typename T>
@@ -596,6 +709,37 @@ __global__ void __launch_bounds__(32 * kGemvCols) k_gemv_t(GemvArgs<T> g) {
   }
 }
 
+// No-transpose product with few columns (a coarse basis, the constraint
+// block): a thread per row, columns in order.  The 8-warp column split of
+// k_gemv_n leaves most warps idle there.
+constexpr int kGemvNarrowCols = 96;   // widest product that takes this kernel
+constexpr int kGemvNarrowRows = 128;  // rows (threads) per CTA
+
+template <typename T>
+__global__ void __launch_bounds__(kGemvNarrowRows) k_gemv_nr(GemvArgs<T> g) {
+  using Acc = typename GemvAcc<T>::type;
+  const int di = gemv_find(g, blockIdx.x);
+  const GemvDesc d = g.desc[di];
+  const int i = (blockIdx.x - g.prefix[di]) * kGemvNarrowRows + threadIdx.x;
+  if (i >= d.m) return;
+  const T* __restrict__ a = g.A + d.a + i;
+  const T* __restrict__ x = g.X + d.x;
+  Acc s;
+  int j = 0;
+  for (; j + 8 <= d.n; j += 8) {
+    T v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = a[(int64_t)(j + u) * d.lda];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s.add(v[u], x[j + u]);
+  }
+  for (; j < d.n; ++j) s.add(a[(int64_t)j * d.lda], x[j]);
+  T v = g.alpha * (T)s.value();
+  T* y = g.Y + d.y;
+  if (g.beta != T(0)) v = fma(g.beta, y[i], v);
+  y[i] = v;
+}
+
 // FP32 products use compensated accumulation, FP64 plain FMA chains.
 template <typename T>
 static void launch_gemv(cudaStream_t st, const GemvArgs<T>& g, unsigned total, bool trans) {
@@ -607,6 +751,10 @@ template <typename T>
 void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& d, int flags,
                   T alpha, T beta, const T* A, const T* X, T* Y) {
   const bool trans = flags & G_TRANS_A;
+  int nmax = 0;
+  for (const auto& x : d) nmax = std::max(nmax, x.n);
+  const bool narrow = !trans && !(flags & (G_TRI_A_LOWER | G_TRI_A_UPPER)) && nmax <= kGemvNarrowCols;
+  const int rows_per_cta = narrow ? kGemvNarrowRows : kGemvRows;
   std::vector<GemvDesc> dd;
   std::vector<int> prefix;
   int64_t total = 0;
@@ -615,7 +763,7 @@ void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& 
     if (outs <= 0) continue;
     dd.push_back(x);
     prefix.push_back((int)total);
-    total += trans ? (outs + kGemvCols - 1) / kGemvCols : (outs + kGemvRows - 1) / kGemvRows;
+    total += trans ? (outs + kGemvCols - 1) / kGemvCols : (outs + rows_per_cta - 1) / rows_per_cta;
   }
   if (dd.empty()) return;
   prefix.push_back((int)total);
@@ -626,8 +774,8 @@ void gemv_batched(cudaStream_t st, DescRing& ring, const std::vector<GemvDesc>& 
   GemvArgs<T> g{reinterpret_cast<const GemvDesc*>(dev),
                 reinterpret_cast<const int*>(dev + dd.size() * sizeof(GemvDesc)),
                 (int)dd.size(), flags, alpha, beta, A, X, Y};
-  launch_gemv<T>(st, g, (unsigned)total, trans);
-
+  if (narrow) k_gemv_nr<T><<<(unsigned)total, kGemvNarrowRows, 0, st>>>(g);
+  else launch_gemv<T>(st, g, (unsigned)total, trans);
   AMB_LAUNCHED();
 }
 
@@ -893,8 +1041,8 @@ void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriD
       }
     }
     if (sa.empty()) continue;
-    gemm_batched<T>(st, ring, sa, G_TRANS_A | G_TRI_A_UPPER | G_TRANS_B, T(1), T(0), zbase, lbase, zbase);
-    gemm_batched<T>(st, ring, sb, G_TRI_A_LOWER | G_TRANS_B, T(-1), T(0), zbase, zbase, zbase);
+    gemm_batched<T>(st, ring, sa, G_TRANS_A | G_TRI_A_UPPER | G_TRANS_B | G_TUNE, T(1), T(0), zbase, lbase, zbase);
+    gemm_batched<T>(st, ring, sb, G_TRI_A_LOWER | G_TRANS_B | G_TUNE, T(-1), T(0), zbase, zbase, zbase);
   }
 }
 

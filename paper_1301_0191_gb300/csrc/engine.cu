@@ -356,13 +356,13 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.ncp[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.ncp[s], 1),
                          std::max(L.nd[s], 1), L.pLD.off[s], L.pCd.off[s], L.pY.off[s]});
-  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER | G_TRANS_B, 1.0, 0.0, dptr<T>(L.LinvD), cdd, dptr<double>(L.Yd));
+  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER | G_TRANS_B | G_TUNE, 1.0, 0.0, dptr<T>(L.LinvD), cdd, dptr<double>(L.Yd));
   // G = Yd^T Yd (FP64, positive semi-definite by construction), Ginvd = G^{-1}
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.ncp[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ncp[s], 1), L.pY.off[s], L.pY.off[s], L.pG.off[s]});
-  gemm_batched<double>(st, ring, d, G_TRANS_A, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(L.Yd), dptr<double>(Gd));
+  gemm_batched<double>(st, ring, d, G_TRANS_A | G_TUNE, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(L.Yd), dptr<double>(Gd));
   DevBuf dgo;
   upload(dgo, L.pG.off, st);
   small_spd_inverse<double>(st, dptr<double>(L.Ginvd), dptr<double>(Gd), dptr<int64_t>(dgo), dptr<int64_t>(L.par), ns,
@@ -381,20 +381,20 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.ncrn[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.nd[s], 1), L.pLD.off[s], pZ.off[s], pZ.off[s]});
-  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER, 1.0, 0.0, dptr<T>(L.LinvD), z2d, dptr<double>(Z3d));
+  gemm_batched<double, T>(st, ring, d, G_TRI_A_LOWER | G_TUNE, 1.0, 0.0, dptr<T>(L.LinvD), z2d, dptr<double>(Z3d));
   // W1 = Yd^T Z3 - [0 | I]
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ncp[s], 1), L.pY.off[s], pZ.off[s], pW.off[s]});
-  gemm_batched<double>(st, ring, d, G_TRANS_A, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(Z3d), dptr<double>(W1d));
+  gemm_batched<double>(st, ring, d, G_TRANS_A | G_TUNE, 1.0, 0.0, dptr<double>(L.Yd), dptr<double>(Z3d), dptr<double>(W1d));
   sub_identity<double>(st, dptr<double>(W1d), dptr<int64_t>(dw), dptr<int64_t>(L.par), ns, imax(L.ncp));
   // Lam = G^{-1} W1
   d.clear();
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.ncp[s], L.nc[s], L.ncp[s], std::max(L.ncp[s], 1), std::max(L.ncp[s], 1),
                          std::max(L.ncp[s], 1), L.pG.off[s], pW.off[s], pW.off[s]});
-  gemm_batched<double>(st, ring, d, 0, 1.0, 0.0, dptr<double>(L.Ginvd), dptr<double>(W1d), dptr<double>(Lamd));
+  gemm_batched<double>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<double>(L.Ginvd), dptr<double>(W1d), dptr<double>(Lamd));
   // Z3 -= Yd Lam
   d.clear();
   for (int s = 0; s < ns; ++s)
@@ -407,7 +407,7 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
   for (int s = 0; s < ns; ++s)
     d.push_back(GemmDesc{L.nd[s], L.nc[s], L.nd[s], std::max(L.nd[s], 1), std::max(L.nd[s], 1),
                          std::max(L.ng[s], 1), L.pLD.off[s], pZ.off[s], L.pPsi.off[s]});
-  gemm_batched<double, T>(st, ring, d, G_TRANS_A | G_TRI_A_UPPER, 1.0, 0.0, dptr<T>(L.LinvD), dptr<double>(Z3d),
+  gemm_batched<double, T>(st, ring, d, G_TRANS_A | G_TRI_A_UPPER | G_TUNE, 1.0, 0.0, dptr<T>(L.LinvD), dptr<double>(Z3d),
                           dptr<double>(PsiD));
   psi_corner_rows<double>(st, dptr<double>(PsiD), dptr<int64_t>(L.par), ns, imax(L.nc));
   convert<T, double>(st, dptr<T>(L.Psi), dptr<double>(PsiD), L.pPsi.total);
@@ -421,8 +421,8 @@ void Engine<T>::coarse_basis(LevelData<T>& L) {
     d2.push_back(GemmDesc{L.nc[s], L.nc[s], L.ng[s], std::max(L.ng[s], 1), std::max(L.ng[s], 1),
                           std::max(L.nc[s], 1), L.pPsi.off[s], pT1.off[s], pT2.off[s]});
   }
-  gemm_batched<double, T>(st, ring, d1, 0, 1.0, 0.0, dptr<T>(L.S), dptr<double>(PsiD), dptr<double>(T1d));
-  gemm_batched<double>(st, ring, d2, G_TRANS_A, 1.0, 0.0, dptr<double>(PsiD), dptr<double>(T1d), dptr<double>(T2d));
+  gemm_batched<double, T>(st, ring, d1, G_TUNE, 1.0, 0.0, dptr<T>(L.S), dptr<double>(PsiD), dptr<double>(T1d));
+  gemm_batched<double>(st, ring, d2, G_TRANS_A | G_TUNE, 1.0, 0.0, dptr<double>(PsiD), dptr<double>(T1d), dptr<double>(T2d));
   coarse_to_double<double>(st, dptr<double>(L.Ac), dptr<double>(T2d), dptr<int64_t>(dt2), dptr<int64_t>(L.par), ns,
                            imax(L.nc));
   AMB_CUDA(cudaStreamSynchronize(st));
@@ -515,7 +515,63 @@ void Engine<T>::setup() {
 // ------------------------------------------------------------------ Algorithm 1
 
 template <typename T>
+void Engine<T>::drop_graph() {
+  if (pgraph) {
+    cudaStreamSynchronize(st);   // a replay may still be running
+    cudaGraphExecDestroy(pgraph);
+  }
+  pgraph = nullptr;
+  pg_r = nullptr;
+  pg_z = nullptr;
+}
+
+template <typename T>
+void Engine<T>::precond(const double* r, double* z) {
+  if (!pgraph || r != pg_r || z != pg_z) {
+    drop_graph();
+    // the graph's descriptor uploads copy from gring's pinned host buffer at
+    // every replay, so gring is written only here and never wraps
+    gring.reset(kGraphRingBytes);
+    // capture on a private stream (the context's stream may be the legacy
+    // NULL stream, which cannot be captured); the graph is launched on the
+    // context's stream, so ordering with the caller's work is unchanged
+    if (!cstream) AMB_CUDA(cudaStreamCreateWithFlags(&cstream, cudaStreamNonBlocking));
+    const cudaStream_t st0 = st;
+    st = cstream;
+    aring = &gring;
+    cudaGraph_t g = nullptr;
+    const int64_t l0 = g_launches;
+    AMB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      apply_level(0, r, z);
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      aring = &ring;
+      st = st0;
+      throw;
+    }
+    const cudaError_t ec = cudaStreamEndCapture(st, &g);
+    aring = &ring;
+    st = st0;
+    AMB_CUDA(ec);
+    // captured kernels did not run: count them at every replay instead
+    pg_kernels = g_launches - l0;
+    g_launches = l0;
+    const cudaError_t e = cudaGraphInstantiate(&pgraph, g, 0);
+    cudaGraphDestroy(g);
+    AMB_CUDA(e);
+    pg_r = r;
+    pg_z = z;
+  }
+  AMB_CUDA(cudaGraphLaunch(pgraph, st));
+  g_launches += pg_kernels;
+  ++pg_replays;
+}
+
+template <typename T>
 void Engine<T>::apply_level(int i, const double* r, double* u) {
+  DescRing& ring = aring ? *aring : this->ring;
   LevelData<T>& L = *lv[i];
   const int ns = L.ns;
   const T one = T(1), zero = T(0);

@@ -41,6 +41,7 @@ class EngineBase {
   virtual int n_levels() const = 0;
   virtual void export_sub(int what, int level, int idx, std::vector<char>& out) = 0;
   virtual double level_factor_flops(int level) const = 0;
+  virtual int64_t graph_replays() const = 0;
 };
 
 // Largest number of substructures per level the staged Schur apply accepts.

@@ -36,6 +36,7 @@ constexpr int kJacobiMax = 112;
 // Threads of the Jacobi kernels: the rotation rounds are FP64-bound on one
 // SM, and 32 warps keep its FP64 pipes busier than 8 (latency hiding).
 constexpr int kJacobiThreads = 1024;
+constexpr int kJacobiMaxBlocks = (kJacobiMax / 2 + 1) * (kJacobiMax / 2 + 2) / 2;   // 2 x 2 blocks of a triangle
 
 // ---------------------------------------------------------------- block helpers
 
@@ -69,6 +70,16 @@ __device__ void jacobi_sweeps(F* A, F* V, int n, int ld, double* red, double* cs
   const int nblk = half * (half + 1) / 2;
   // rotations below this relative size are skipped (FP64: far below rounding)
   const double skip = sizeof(F) == 8 ? 1e-18 : 1e-9;
+  // block (k, l), k <= l, of each triangular index, decoded once
+  __shared__ uint16_t bk[kJacobiMaxBlocks], bl[kJacobiMaxBlocks];
+  for (int idx = tid; idx < nblk; idx += nt) {
+    int l = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
+    while (l * (l + 1) / 2 > idx) --l;
+    while ((l + 1) * (l + 2) / 2 <= idx) ++l;
+    bl[idx] = (uint16_t)l;
+    bk[idx] = (uint16_t)(idx - l * (l + 1) / 2);
+  }
+  __syncthreads();
   for (int sweep = 0; sweep < maxs; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = tid; idx < n * n; idx += nt) {
@@ -87,13 +98,27 @@ __device__ void jacobi_sweeps(F* A, F* V, int n, int ld, double* red, double* cs
         int p = a < b ? a : b, q = a < b ? b : a;
         F c = F(1), s = F(0);
         if (q < n) {
-          F apq = A[p + q * ld];
-          F app = A[p + p * ld], aqq = A[q + q * ld];
-          if (fabs((double)apq) > 1e-300 && fabs((double)apq) > skip * sqrt(fabs((double)app * (double)aqq))) {
-            F th = (aqq - app) / (F(2) * apq);
-            F t = (th >= F(0) ? F(1) : F(-1)) / (F(fabs((double)th)) + F(sqrt((double)th * (double)th + 1.0)));
-            c = F(1) / F(sqrt((double)t * (double)t + 1.0));
-            s = t * c;
+          const F apq = A[p + q * ld];
+          const F app = A[p + p * ld], aqq = A[q + q * ld];
+          if constexpr (sizeof(F) == 8) {
+            if (fabs(apq) > 1e-300 && fabs(apq) > skip * sqrt(fabs(app * aqq))) {
+              const F th = (aqq - app) / (F(2) * apq);
+              const F t = (th >= F(0) ? F(1) : F(-1)) / (fabs(th) + sqrt(th * th + F(1)));
+              c = F(1) / sqrt(t * t + F(1));
+              s = t * c;
+            }
+          } else {
+            // FP32 sweeps: the angle in FP64 arithmetic.  (Single-precision
+            // angles are faster, but the FP32 form's pair eigenproblems are
+            // sensitive to which of the equally accurate FP64 end states the
+            // refinement reaches: on the 1e4-contrast channels workload that
+            // variant lost an eigenvalue of one pair.)
+            if (fabs((double)apq) > 1e-300 && fabs((double)apq) > skip * sqrt(fabs((double)app * (double)aqq))) {
+              const F th = (aqq - app) / (F(2) * apq);
+              const F t = (th >= F(0) ? F(1) : F(-1)) / (F(fabs((double)th)) + F(sqrt((double)th * (double)th + 1.0)));
+              c = F(1) / F(sqrt((double)t * (double)t + 1.0));
+              s = t * c;
+            }
           }
         }
         P[k] = p;
@@ -104,11 +129,7 @@ __device__ void jacobi_sweeps(F* A, F* V, int n, int ld, double* red, double* cs
       __syncthreads();
       for (int idx = tid; idx < nblk + n * half; idx += nt) {
         if (idx < nblk) {
-          // block (k, l), k <= l, from the triangular index
-          int l = (int)((sqrtf(8.f * idx + 1.f) - 1.f) * 0.5f);
-          while (l * (l + 1) / 2 > idx) --l;
-          while ((l + 1) * (l + 2) / 2 <= idx) ++l;
-          const int k = idx - l * (l + 1) / 2;
+          const int k = bk[idx], l = bl[idx];
           const F sk = (F)sn[k], sl = (F)sn[l];
           if (sk == F(0) && sl == F(0)) continue;
           const F ck = (F)cs[k], cl = (F)cs[l];
@@ -1039,7 +1060,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
                              q[Q_OF] + side * (int64_t)nf * nf, q[Q_OJ] + side * (int64_t)nf * m,
                              q[Q_OJ] + (2 + side) * (int64_t)nf * m});
     }
-    gemm_batched<V, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(Sff), dptr<V>(Jb), dptr<V>(Jb));
+    gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(Sff), dptr<V>(Jb), dptr<V>(Jb));
     k_lob_iet<V, V><<<dim3(np, m), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, dptr<V>(Jb), m, dptr<int32_t>(dps),
                                                 dptr<int32_t>(dpt), dptr<double>(dws), dptr<double>(dwt));
     AMB_LAUNCHED();
@@ -1060,7 +1081,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
                              q[Q_OQ] + cout * m * N + r0});
       }
     }
-    gemm_batched<V, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+    gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
     
     project(Q, Q_OQ, cout * m, m);
   };
@@ -1114,11 +1135,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       const unsigned gx = (unsigned)std::min<int64_t>(nblk((int64_t)imax(L.nd) * m), 64);
       k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Xs), dptr<T>(Oin), dmap, m, 1);
       AMB_LAUNCHED();
-      gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER, one, zero, dptr<T>(L.LinvD), dptr<T>(Xs), dptr<T>(Zb));
-      gemm_batched<T>(st, ring, d2, G_TRANS_A, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
+      gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Xs), dptr<T>(Zb));
+      gemm_batched<T>(st, ring, d2, G_TRANS_A | G_TUNE, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
       gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
       gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
-      gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), dptr<T>(Xs));
+      gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), dptr<T>(Xs));
       k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Oout), dptr<T>(Xs), dmap, m, 0);
       AMB_LAUNCHED();
     }
@@ -1136,7 +1157,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
         co += (int64_t)nc * m;
       }
     }
-    gemm_batched<T>(st, ring, dc1, G_TRANS_A, one, zero, dptr<T>(L.Psi), dptr<T>(Oin), dptr<T>(Cb));
+    gemm_batched<T>(st, ring, dc1, G_TRANS_A | G_TUNE, one, zero, dptr<T>(L.Psi), dptr<T>(Oin), dptr<T>(Cb));
     k_lob_cgather<T><<<np, 256, 0, st>>>(dptr<T>(Cb), QPd, m, dptr<int32_t>(dcms), dptr<int32_t>(dcmt));
     AMB_LAUNCHED();
     for (int p = 0; p < np; ++p) {
@@ -1198,8 +1219,8 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
         dx.push_back(GemmDesc{(int)N, m, m, (int)N, m3, (int)N, u, q[Q_OCC], t});
       }
     }
-    gemm_batched<V>(st, ring, dp, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
-    gemm_batched<V>(st, ring, dx, 0, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
+    gemm_batched<V>(st, ring, dp, G_TUNE, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
+    gemm_batched<V>(st, ring, dx, G_TUNE, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     k_lob_copyback<V><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<V>(Tp), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
   };

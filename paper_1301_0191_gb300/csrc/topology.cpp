@@ -78,7 +78,12 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
     for (size_t r = 0; r < ord.size(); ++r) rk[ord[r]] = (int)r;
     for (int i : order) rank[i] = rk[sid[i]];
   }
-  // corner rule: alone in its (sharing set, tags) class
+  // corner rule: a vertex of the box grid (with b boundary bits, shared by
+  // 2^(3-b) substructures) that is alone in its (sharing set, tags) class
+  auto box_vertex = [&](int i) {
+    const int nb = __builtin_popcount((unsigned)N.tags[i] & 63u);
+    return nb <= 3 && N.nsub(i) == (1 << (3 - nb));
+  };
   std::sort(order.begin(), order.end(), [&](int a, int b) {
     if (rank[a] != rank[b]) return rank[a] < rank[b];
     return N.tags[a] != N.tags[b] ? N.tags[a] < N.tags[b] : a < b;
@@ -86,7 +91,7 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
   for (size_t r = 0; r < order.size();) {
     size_t e = r + 1;
     while (e < order.size() && rank[order[r]] == rank[order[e]] && N.tags[order[r]] == N.tags[order[e]]) ++e;
-    if (e == r + 1 && N.eligible[order[r]]) corner[order[r]] = 1;
+    if (e == r + 1 && N.eligible[order[r]] && box_vertex(order[r])) corner[order[r]] = 1;
     r = e;
   }
   // remaining interface nodes grouped by sharing set: sets in lexicographic
@@ -462,11 +467,7 @@ LevelTopo build_level_next(const LevelTopo& prev, const int32_t* parent, int n_s
     N.subs.insert(N.subs.end(), ps.begin(), ps.end());
     N.soff.push_back((int)N.subs.size());
     N.tags[o] = ob.tags;
-    // a level-i corner is a box vertex of level i+1 when every direction in
-    // which it is not on the domain boundary is a cut of level i+1, i.e. when
-    // 2^(3 - #boundary bits) level-(i+1) substructures share it
-    const int nb = __builtin_popcount((unsigned)ob.tags & 63u);
-    N.eligible[o] = ob.kind == OBJ_CORNER && nb <= 3 && (int)ps.size() == (1 << (3 - nb));
+    N.eligible[o] = ob.kind == OBJ_CORNER;
     for (size_t q = 0; q < ob.dofs.size(); ++q) {
       N.dofs.push_back(ob.first + (int64_t)q);
       N.comps.push_back(ob.comps[q]);

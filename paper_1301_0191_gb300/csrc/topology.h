@@ -2,15 +2,17 @@
 //
 // Interface = nodes shared by >= 2 substructures; faces = nodes shared by
 // the same two substructures; edges = nodes shared by the same set of more
-// than two.  Corners: an interface node whose (sharing set, boundary-face
-// tags) class contains that node alone; for box partitions these are the
-// vertices of the box grid (every coordinate on a cut plane or on the
-// domain boundary), minus Dirichlet nodes.  On level i >= 2 the nodes are
-// the coarse objects of level i-1; a level-(i-1) corner becomes a corner
-// when it is a vertex of the level-i box grid: with b boundary bits, it is
-// shared by 2^(3-b) level-i substructures.  (A level-(i-1) corner on the
-// domain boundary inside a level-i face is alone in its class, because the
-// face objects around it carry no boundary bits, but it is no box vertex.)
+// than two.  Corners are the vertices of the box grid (every coordinate on a
+// cut plane or on the domain boundary), minus Dirichlet nodes.  The library
+// sees only the element partition, so it uses the topological equivalent for
+// box partitions: a node with b domain-boundary bits is a box vertex when
+// 2^(3-b) substructures share it, and it must also be alone in its (sharing
+// set, boundary bits) class.  "Alone in its class" by itself is not enough:
+// next to a Dirichlet face a two-element segment leaves a face one node
+// wide, whose node on the domain boundary is alone in its class but no
+// vertex.  On level i >= 2 the nodes are the coarse objects of level i-1 and
+// only level-(i-1) corners may become corners (under the same rule, with the
+// level-i sharing sets).
 #pragma once
 
 #include <array>
