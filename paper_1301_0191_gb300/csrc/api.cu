@@ -158,6 +158,7 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
               "poisson_ratio out of range");
     c->opt = *opt;
     c->st = static_cast<cudaStream_t>(opt->cuda_stream);
+    alloc_stream() = c->st;
     AMB_CUDA(cudaGetDevice(&c->device));
     Mesh& m = c->mesh;
     m.nx = mesh->nx;
@@ -449,6 +450,7 @@ void amb_destroy(amb_ctx* c) {
   if (!c) return;
   if (c->st) cudaStreamSynchronize(c->st);
   else cudaDeviceSynchronize();
+  alloc_stream() = c->st;
   delete c;
 }
 

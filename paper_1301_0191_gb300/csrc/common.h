@@ -42,6 +42,17 @@ extern thread_local int64_t g_launches;
     AMB_CUDA(cudaGetLastError());            \
   } while (0)
 
+// Device memory comes from the device's stream-ordered pool (cudaMallocAsync)
+// with no release threshold: buffers freed by one context are reused by the
+// next without returning to the driver, and a free does not synchronize the
+// device (cudaFree does).  Allocations and frees are ordered on the stream of
+// the context that the calling thread is serving (set at every ABI entry).
+inline cudaStream_t& alloc_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+void pool_init();
+
 // Owned device allocation.
 struct DevBuf {
   void* p = nullptr;
@@ -56,18 +67,19 @@ struct DevBuf {
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, alloc_stream());
     p = nullptr;
     bytes = 0;
   }
   void alloc(size_t n) {
     release();
     if (n == 0) n = 16;
-    cudaError_t e = cudaMalloc(&p, n);
+    pool_init();
+    cudaError_t e = cudaMallocAsync(&p, n, alloc_stream());
     if (e != cudaSuccess) {
       p = nullptr;
       (void)cudaGetLastError();
-      throw Error(AMB_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
+      throw Error(AMB_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e));
     }
     bytes = n;
   }

@@ -47,6 +47,7 @@ template <typename F>
 int guarded(amb_ctx* c, F&& fn) {
   if (!c) return AMB_EINVAL;
   const int64_t l0 = g_launches;
+  alloc_stream() = c->st;
   try {
     c->err.clear();
     fn();

@@ -20,6 +20,18 @@ namespace amb {
 
 thread_local int64_t g_launches = 0;
 
+void pool_init() {
+  static thread_local int done_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev == done_dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  done_dev = dev;
+}
+
 // ------------------------------------------------------------------ GEMM
 
 template <typename T> struct Vec2;
