@@ -91,29 +91,59 @@ __device__ __forceinline__ float tf32_round(float x) {
 // source block (rows x cols; column form: (r, k) at src + r + k*ld, K-major
 // form: src + k + r*ld) -> slab rows [row0, row0 + rpad), K-contiguous,
 // stride kp; entries outside rows x cols or outside the triangle are zero.
-// 32 x 32 tiles through shared memory (coalesced on both sides).
-__global__ void k_tc_split(const TcSplitDesc* d, int kp, float* sh, float* sl) {
-  __shared__ float t[32][33];
+// A CTA moves a 128-row x 32-column tile through shared memory: the reads
+// are coalesced along the source's contiguous direction, and each thread
+// writes four consecutive K values of one slab row with a 16-byte store
+// (slab rows are 1 KB apart, K blocks 128 B).
+constexpr int kSplitRows = 128;
+
+__global__ void __launch_bounds__(256) k_tc_split(const TcSplitDesc* d, int kp, float* sh, float* sl) {
+  __shared__ float t[32][kSplitRows + 1];   // [k][r]
   const TcSplitDesc x = d[blockIdx.z];
-  const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 32;
+  const int r0 = blockIdx.x * kSplitRows, k0 = blockIdx.y * 32;
   if (r0 >= x.rpad || k0 >= kp) return;
-  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-  for (int q = ty; q < 32; q += 8) {
-    // column form: lane = row; K-major form: lane = k (t is [k][r] either way)
-    const int r = x.kmajor ? r0 + q : r0 + tx, k = x.kmajor ? k0 + tx : k0 + q;
-    bool ok = r < x.rows && k < x.cols;
-    if (x.tri == 1 && k - r > x.diag) ok = false;
-    if (x.tri == 2 && k - r < x.diag) ok = false;
-    const float v = ok ? (x.kmajor ? x.src[k + (int64_t)r * x.ld] : x.src[r + (int64_t)k * x.ld]) : 0.f;
-    if (x.kmajor) t[tx][q] = v; else t[q][tx] = v;
+  const int tid = threadIdx.x;
+  if (x.kmajor) {
+    // lane = k: 32 consecutive k of one row per warp instruction
+    const int k = k0 + (tid & 31);
+    for (int rr = tid >> 5; rr < kSplitRows; rr += 8) {
+      const int r = r0 + rr;
+      bool ok = r < x.rows && k < x.cols;
+      if (x.tri == 1 && k - r > x.diag) ok = false;
+      if (x.tri == 2 && k - r < x.diag) ok = false;
+      t[tid & 31][rr] = ok ? x.src[k + (int64_t)r * x.ld] : 0.f;
+    }
+  } else {
+    // lane = row: 128 consecutive rows of one column per 4 warp instructions
+    for (int idx = tid; idx < 32 * kSplitRows; idx += 256) {
+      const int rr = idx % kSplitRows, kk = idx / kSplitRows;
+      const int r = r0 + rr, k = k0 + kk;
+      bool ok = r < x.rows && k < x.cols;
+      if (x.tri == 1 && k - r > x.diag) ok = false;
+      if (x.tri == 2 && k - r < x.diag) ok = false;
+      t[kk][rr] = ok ? x.src[r + (int64_t)k * x.ld] : 0.f;
+    }
   }
   __syncthreads();
-  for (int q = ty; q < 32; q += 8) {
-    const float v = t[tx][q];
-    const float h = tf32_round(v);
-    const int64_t o = (x.row0 + r0 + q) * (int64_t)kp + k0 + tx;
-    sh[o] = h;
-    sl[o] = tf32_round(v - h);
+  // 128 rows x 8 groups of 4 k: thread -> (row, k group)
+  for (int idx = tid; idx < kSplitRows * 8; idx += 256) {
+    const int g = idx & 7, rr = idx >> 3;
+    float4 h, l;
+    float v = t[4 * g + 0][rr];
+    h.x = tf32_round(v);
+    l.x = tf32_round(v - h.x);
+    v = t[4 * g + 1][rr];
+    h.y = tf32_round(v);
+    l.y = tf32_round(v - h.y);
+    v = t[4 * g + 2][rr];
+    h.z = tf32_round(v);
+    l.z = tf32_round(v - h.z);
+    v = t[4 * g + 3][rr];
+    h.w = tf32_round(v);
+    l.w = tf32_round(v - h.w);
+    const int64_t o = (x.row0 + r0 + rr) * (int64_t)kp + k0 + 4 * g;
+    *reinterpret_cast<float4*>(sh + o) = h;
+    *reinterpret_cast<float4*>(sl + o) = l;
   }
 }
 
@@ -410,7 +440,8 @@ void run_tiles(cudaStream_t st, DescRing& ring, const std::vector<TcSplitDesc>& 
   float* sh = tc_slab((size_t)rows * kp);
   float* sl = sh + (size_t)rows * kp;
   const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(spr.data(), spr.size() * sizeof(TcSplitDesc), st));
-  k_tc_split<<<dim3((unsigned)(maxr / 32), kp / 32, (unsigned)spr.size()), dim3(32, 8), 0, st>>>(dsp, kp, sh, sl);
+  static_assert(kTM % kSplitRows == 0, "slab row padding must cover whole split tiles");
+  k_tc_split<<<dim3((unsigned)(maxr / kSplitRows), kp / 32, (unsigned)spr.size()), 256, 0, st>>>(dsp, kp, sh, sl);
   AMB_LAUNCHED();
   std::vector<char> blob(td.size() * sizeof(TcDesc) + prefix.size() * sizeof(int));
   memcpy(blob.data(), td.data(), td.size() * sizeof(TcDesc));
