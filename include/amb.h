@@ -195,8 +195,8 @@ int amb_load_vector(amb_ctx* ctx, const double* body, double* f);
  * columns) and the last solve. */
 int amb_eigen_report(const amb_ctx* ctx, amb_report* buf, size_t* nbytes);
 
-/* Adjoint gradient d q / d log(coeff_e) for every element (north-star
- * addition, not in the paper): solve A lambda = dq/du with the same PCG and
+/* Adjoint gradient d q / d log(coeff_e) for every element (an addition
+ * to the method, not in the paper): solve A lambda = dq/du with the same PCG and
  * preconditioner (lambda = u of the last solve for AMB_QOI_COMPLIANCE, no
  * second solve), then g_e = -coeff_e lambda_e^T Khat u_e.  Needs a previous
  * amb_solve.  dq_du [host|device] full-grid nodal (NULL for compliance);

@@ -1,7 +1,8 @@
 // Batched dense kernels of the substructure engine: variable-size batched
-// GEMM (with triangular operands and lower-only output), batched GEMV,
-// blocked right-looking partial Cholesky and recursive-doubling triangular
-// inverse.  These carry the factorizations of Sec. 2 / Sec. 5 (A_II = L L^T,
+// GEMM (with triangular operands and lower-only output, tile shape chosen by
+// timing for repeatable calls), batched GEMV, blocked right-looking partial
+// Cholesky and recursive-doubling triangular inverse.  Device memory comes
+// from the stream-ordered pool (pool_init).  These carry the factorizations of Sec. 2 / Sec. 5 (A_II = L L^T,
 // S = K_GG - X^T X with X = L^{-1} K_IG, and the corner-constrained Neumann
 // factor S_DD = L_D L_D^T) and every solve with those factors.
 #include <algorithm>

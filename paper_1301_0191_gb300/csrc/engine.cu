@@ -15,6 +15,8 @@
 //   * coarse basis from eq. local_saddle_point_problem with corners primal:
 //     Y = L_D^{-1} C_D^T, G = Y^T Y, Psi, and the coarse matrix Psi^T S Psi
 //     (= -mu, the level-(i+1) element matrix).
+// Algorithm 1 on all levels is captured once per context as a CUDA graph and
+// replayed for every PCG iteration (precond).
 #include <cmath>
 #include <map>
 

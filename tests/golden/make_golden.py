@@ -47,8 +47,8 @@ def golden(index):
 
 
 def gradient_golden(index=4, n_samples=512):
-    """Compliance Q = f^T u and its adjoint gradient dQ/dlog(kappa_e) (the
-    spec gradient: lambda = u) at seeded sample elements.  u comes from
+    """Compliance Q = f^T u and its adjoint gradient dQ/dlog(kappa_e) (for the
+    compliance the adjoint is lambda = u) at seeded sample elements.  u comes from
     the oracle's two-level BDDC + PCG without adaptive constraints at rtol
     1e-12 (the gradient does not depend on the preconditioner; a sparse LU of
     the 270,400-dof system takes far longer)."""

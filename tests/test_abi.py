@@ -38,3 +38,13 @@ def test_binding_structs_match_header_sizes():
     assert ctypes.sizeof(B.PairReport) == 8 * 4 + 16 * 8 + 8
     o = B.default_options()
     assert o.precision == B.FP64 and o.max_adaptive_per_face == 10 and o.pcg_rtol == 1e-8
+
+
+def test_kernel_stats_fields_follow_the_header():
+    from paper_1301_0191_gb300 import binding as B
+    src = open(os.path.join(ROOT, "include", "amb.h")).read()
+    body = src[src.index("typedef struct {\n  double ms[AMB_FAM_N];"):src.index("} amb_kernel_stats;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = re.findall(r"(?:double|int64_t)\s+([a-z_]+)", body)
+    assert names == [f[0] for f in B.KernelStats._fields_]
+    assert ctypes.sizeof(B.KernelStats) == 8 * (4 * B.FAM_N + 8 + 4)

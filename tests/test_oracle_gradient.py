@@ -1,4 +1,4 @@
-"""Pins of the adjoint gradient (spec addition, not in the paper):
+"""Pins of the adjoint gradient (an addition to the method, not in the paper):
 central finite differences in log-coefficient space."""
 import numpy as np
 import pytest

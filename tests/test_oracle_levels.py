@@ -83,3 +83,32 @@ def test_classification_counts_2x2x2():
     assert len(lev.faces) == 12
     # every edge is shared by 4 substructures, every face by 2
     assert all(len(k) == 4 for k in lev.edges)
+
+
+def test_box_vertex_corners_ragged_and_level_two():
+    """Corner counts by the box-vertex rule, counted by hand from the cut
+    planes.  Ragged 3 x 2 x 1 boxes (x cuts 0, 2, 5, 9; y cuts 0, 4, 9; one z
+    box) with the Dirichlet face x = 0: vertices on x = 2 and x = 5 (y = 0,
+    4, 9; z = 0, 9) are interface nodes, on x = 9 only y = 4 is (shared by
+    two boxes) -> 6 + 6 + 2 = 14.  The face between the boxes (0,0) and
+    (0,1) is one node wide (x = 1); its nodes on z = 0 and z = 9 are no
+    vertices.  Level 2 of the 4 x 2 x 1 toy grouped 2 x 1 x 1: the level-2
+    vertices on the shared plane x = 6 are (y, z) in {0, 6} x {0, 3} -> 4
+    corners; the level-1 corners at y = 3 are not."""
+    rng = np.random.default_rng(np.random.PCG64(21))
+    coeff = np.exp(rng.standard_normal(9 ** 3))
+    prob = ai._make("ragged", 9, None, 1, coeff, 2, 3.0,
+                    cuts1=[np.array([0, 2, 5, 9]), np.array([0, 4, 9]), np.array([0, 9])])
+    lev = lv.level_one(prob)
+    assert int(lev.node_corner.sum()) == 14
+    n1 = prob.nx + 1
+    for z in (0, 9):
+        node = 1 + n1 * (4 + n1 * z)
+        assert lev.node_interface[node] and not lev.node_corner[node]
+    groups = [np.array([0, 2, 4]), np.array([0, 2]), np.array([0, 1])]
+    toy = ai.toy(3, 3, 41, split=(4, 2, 1), levels=3, groups=groups, sigma=1.0, tau=2.0)
+    from oracle import solver
+    h = solver.Hierarchy(toy)
+    # level 1 (cuts x 0,3,6,9,12; y 0,3,6; z 0,3): x = 3, 6, 9 give 3 x 3 x 2 = 18, x = 12 only y = 3 -> 20
+    assert int(h.levels[0].node_corner.sum()) == 20
+    assert int(h.levels[1].node_corner.sum()) == 4
