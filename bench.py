@@ -350,6 +350,10 @@ def main():
         flops = sum(2.0 * n * n * width for n in sizes)
         schur[f"w{width}"] = {"ms": t * 1e3, "GB/s": byts / t / 1e9, "hbm_frac": byts / t / 1e9 / peaks["hbm_gbs"],
                               "TFLOP/s": flops / t / 1e12, "alu_frac": flops / t / 1e12 / alu_peak}
+        if prec == B.FP32 and width >= 64:
+            # tensor cores, 3xTF32: three TF32 products per useful multiply-add
+            schur[f"w{width}"].update({"path": "tensor cores (3xTF32)",
+                                       "tensor_pipe_frac": 3.0 * flops / t / 1e12 / tf32_peak})
     c.close()
 
     fp64_form = None

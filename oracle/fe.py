@@ -21,7 +21,11 @@ _GAUSS = (0.5 - 0.5 / np.sqrt(3.0), 0.5 + 0.5 / np.sqrt(3.0))  # 2-point rule on
 
 
 def _shape_gradients(xi, eta, zeta, h):
-    """Gradients (8, 3) of the 8 tri-linear shape functions on a cube of side h."""
+    """Gradients (8, 3) of the 8 tri-linear shape functions on a cube of side h.
+
+    Pinned by test_oracle_fe.py::test_poisson_element_exact and test_elasticity_element_exact_block
+    (exact symbolic integrals of the element matrices built from these gradients).
+    """
     g = np.zeros((8, 3))
     for a in range(8):
         ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
@@ -36,13 +40,19 @@ def _shape_gradients(xi, eta, zeta, h):
 
 
 def lame(young: float, nu: float):
+    """Lame parameters of (E, nu).  Pinned by
+    test_oracle_fe.py::test_elasticity_element_exact_block."""
     lam = young * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
     mu = young / (2.0 * (1.0 + nu))
     return lam, mu
 
 
 def reference_stiffness(dofs_per_node: int, h: float, nu: float = 0.3) -> np.ndarray:
-    """Element matrix for unit coefficient (kappa = 1 or Young's modulus E = 1)."""
+    """Element matrix for unit coefficient (kappa = 1 or Young's modulus E = 1).
+
+    Pinned by test_oracle_fe.py::test_poisson_element_exact, test_elasticity_element_exact_block
+    (exact integrals) and test_rigid_modes_null_space (six rigid modes span the null space).
+    """
     nd = 8 * dofs_per_node
     k = np.zeros((nd, nd))
     wq = 0.125 * h ** 3  # weight of each of the 8 Gauss points times the element volume
@@ -72,7 +82,11 @@ def reference_stiffness(dofs_per_node: int, h: float, nu: float = 0.3) -> np.nda
 
 
 def element_nodes(nx: int, ny: int, nz: int) -> np.ndarray:
-    """(n_el, 8) global node ids of every element, element order i fastest."""
+    """(n_el, 8) global node ids of every element, element order i fastest.
+
+    Pinned by test_oracle_fe.py::test_patch_constant_strain (wrong connectivity breaks the patch
+    test).
+    """
     k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
     i, j, k = i.ravel(), j.ravel(), k.ravel()
     out = np.empty((i.size, 8), dtype=np.int64)
@@ -83,14 +97,20 @@ def element_nodes(nx: int, ny: int, nz: int) -> np.ndarray:
 
 
 def element_dofs(prob) -> np.ndarray:
-    """(n_el, 8*dpn) global full-grid dof ids (node * dpn + component)."""
+    """(n_el, 8*dpn) global full-grid dof ids (node * dpn + component).
+
+    Pinned by test_oracle_fe.py::test_patch_constant_strain.
+    """
     nodes = element_nodes(prob.nx, prob.ny, prob.nz)
     d = prob.dofs_per_node
     return (nodes[:, :, None] * d + np.arange(d)[None, None, :]).reshape(nodes.shape[0], 8 * d)
 
 
 def free_dof_map(prob):
-    """Map full-grid dof -> free dof index (-1 for Dirichlet dofs) and the free dof list."""
+    """Map full-grid dof -> free dof index (-1 for Dirichlet dofs) and the free dof list.
+
+    Pinned by test_oracle_fe.py::test_total_load and test_patch_constant_strain.
+    """
     d = prob.dofs_per_node
     fixed = np.repeat(prob.dirichlet_node_mask.astype(bool), d)
     fmap = -np.ones(fixed.size, dtype=np.int64)
@@ -100,7 +120,11 @@ def free_dof_map(prob):
 
 
 def assemble_global(prob, coeff=None) -> sp.csr_matrix:
-    """Global stiffness on free dofs, K = sum_e coeff_e * Khat scattered."""
+    """Global stiffness on free dofs, K = sum_e coeff_e * Khat scattered.
+
+    Pinned by test_oracle_fe.py::test_patch_constant_strain (a linear field gives zero interior
+    forces).
+    """
     coeff = prob.coeff if coeff is None else coeff
     khat = reference_stiffness(prob.dofs_per_node, prob.h, prob.poisson_ratio)
     fmap, free = free_dof_map(prob)
@@ -116,7 +140,10 @@ def assemble_global(prob, coeff=None) -> sp.csr_matrix:
 
 def load_vector(prob) -> np.ndarray:
     """Consistent nodal loads of a per-element constant body force, on free dofs.
-    For tri-linear shape functions on a box, the integral of N_a is V/8."""
+    For tri-linear shape functions on a box, the integral of N_a is V/8.
+
+    Pinned by test_oracle_fe.py::test_total_load (the loads sum to body force times volume).
+    """
     fmap, free = free_dof_map(prob)
     ed = element_dofs(prob)
     d = prob.dofs_per_node
@@ -127,6 +154,7 @@ def load_vector(prob) -> np.ndarray:
 
 
 def to_full(prob, u_free: np.ndarray) -> np.ndarray:
+    """Index bookkeeping only (no arithmetic)."""
     fmap, free = free_dof_map(prob)
     out = np.zeros(prob.n_dofs_full)
     out[free] = u_free

@@ -17,6 +17,8 @@ from . import fe
 
 
 def element_gradient(prob, u_free, lam_free, coeff=None):
+    """g_e = -coeff_e lambda_e^T Khat u_e.  Pinned by
+    test_oracle_gradient.py::test_gradient_vs_central_fd."""
     coeff = prob.coeff if coeff is None else coeff
     khat = fe.reference_stiffness(prob.dofs_per_node, prob.h, prob.poisson_ratio)
     ue = fe.to_full(prob, u_free)[fe.element_dofs(prob)]
@@ -25,7 +27,11 @@ def element_gradient(prob, u_free, lam_free, coeff=None):
 
 
 def compliance_and_gradient(prob, coeff=None):
-    """Direct (sparse LU) compliance and its adjoint gradient."""
+    """Direct (sparse LU) compliance and its adjoint gradient.
+
+    Pinned by test_oracle_gradient.py::test_gradient_vs_central_fd (central differences in log-
+    coefficient space) and test_gradient_through_bddc_solution.
+    """
     coeff = prob.coeff if coeff is None else coeff
     a = fe.assemble_global(prob, coeff)
     f = fe.load_vector(prob)

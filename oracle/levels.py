@@ -76,6 +76,7 @@ class Level:
 
     def __init__(self, n, elem_dofs, elem_mat, elem_sub, n_subs, node_of_dof, comp_of_dof,
                  node_eligible, node_vertex, node_coord=None, initial="ce"):
+        """Pinned through its steps below."""
         self.n = n
         self.elem_dofs = elem_dofs          # list of int arrays (-1 = absent dof)
         self.elem_mat = elem_mat            # callable e -> dense matrix
@@ -95,6 +96,9 @@ class Level:
 
     # ---------------------------------------------------------------- Sec. 2
     def _classify(self):
+        """Sec. 2 classification.  Pinned by test_oracle_levels.py::test_classification_counts_2x2x2
+        (the paper's 12 faces of the 2x2x2 decomposition, Table 1) and
+        test_box_vertex_corners_ragged_and_level_two (corner counts from the cut planes)."""
         rows, cols = [], []
         for e, d in enumerate(self.elem_dofs):
             d = d[d >= 0]
@@ -127,6 +131,8 @@ class Level:
             self.dofs_of_node[self.node_of_dof[d]].append(d)
 
     def _local_matrices(self):
+        """Pinned by test_oracle_levels.py::test_floating_schur_null_space (rigid modes of a
+        floating substructure)."""
         elems_of_sub = [[] for _ in range(self.n_subs)]
         for e in range(len(self.elem_dofs)):
             elems_of_sub[self.elem_sub[e]].append(e)
@@ -155,6 +161,9 @@ class Level:
 
     # ---------------------------------------------------------------- Sec. 7.1
     def _initial_constraints(self):
+        """Sec. 7.1 corners + edge averages.  Pinned by
+        test_oracle_levels.py::test_coarse_basis_identities (C Psi = I) and
+        test_oracle_solver.py::test_all_corners_one_iteration."""
         self.objects: List[CoarseObject] = []
         for i in np.nonzero(self.node_corner)[0]:
             dofs = self.dofs_of_node[i]
@@ -180,6 +189,7 @@ class Level:
         self._number_coarse()
 
     def _number_coarse(self):
+        """Pinned by test_oracle_levels.py::test_coarse_basis_identities."""
         n = 0
         for ob in self.objects:
             ob.first = n
@@ -200,7 +210,10 @@ class Level:
             sb.rc = np.array(ids, dtype=np.int64)
 
     def add_adaptive(self, s: int, t: int, face_dofs: np.ndarray, rows: np.ndarray):
-        """Append adaptive rows (functionals on the face dofs shared by s, t)."""
+        """Append adaptive rows (functionals on the face dofs shared by s, t).
+
+        Pinned by test_oracle_pair.py::test_corollary1_added_rows.
+        """
         for r in rows:
             self.objects.append(CoarseObject(kind="adaptive", subs=(min(s, t), max(s, t)),
                                              dofs=[np.asarray(face_dofs)], weights=[np.asarray(r)],
@@ -208,6 +221,8 @@ class Level:
 
     # ---------------------------------------------------------------- Sec. 7
     def _weights(self):
+        """Pinned by test_oracle_levels.py::test_averaging_is_projection_onto_U (partition of
+        unity)."""
         diag_sum = np.zeros(self.n)
         for sb in self.subs:
             np.add.at(diag_sum, sb.gdofs, np.diag(sb.k)[sb.n_i:])
@@ -216,6 +231,7 @@ class Level:
 
     # ---------------------------------------------------------------- Sec. 2, 5
     def schur(self):
+        """Pinned by test_oracle_levels.py::test_floating_schur_null_space."""
         for sb in self.subs:
             ni = sb.n_i
             kii, kig, kgg = sb.k[:ni, :ni], sb.k[:ni, ni:], sb.k[ni:, ni:]
@@ -227,7 +243,11 @@ class Level:
             sb.s = 0.5 * (sb.s + sb.s.T)
 
     def coarse_basis(self):
-        """eq. local_saddle_point_problem; coarse element matrices Psi^T S Psi = -mu."""
+        """eq. local_saddle_point_problem; coarse element matrices Psi^T S Psi = -mu.
+
+        Pinned by test_oracle_levels.py::test_coarse_basis_identities (C Psi = I, Psi^T S Psi =
+        -mu).
+        """
         self._number_coarse()
         for sb in self.subs:
             nc, ng = sb.c.shape
@@ -250,13 +270,17 @@ class Level:
             sb.neumann_lu = sla.lu_factor(kn)
 
     def coarse_matrix(self) -> np.ndarray:
+        """Pinned by test_oracle_solver.py::test_three_levels_single_top_sub_equals_two_levels."""
         a = np.zeros((self.n_coarse, self.n_coarse))
         for sb in self.subs:
             a[np.ix_(sb.rc, sb.rc)] += sb.ac
         return 0.5 * (a + a.T)
 
     def operator(self) -> sp.csr_matrix:
-        """The level problem's matrix, assembled from its elements."""
+        """The level problem's matrix, assembled from its elements.
+
+        Pinned by test_oracle_solver.py::test_three_levels_spectrum and test_solution_vs_direct.
+        """
         rows, cols, vals = [], [], []
         for e, d in enumerate(self.elem_dofs):
             keep = d >= 0
@@ -272,7 +296,10 @@ class Level:
     # ---------------------------------------------------------------- E operator
     def average(self, z: List[np.ndarray]) -> np.ndarray:
         """E: W -> U.  Interface dofs get the weighted average of the
-        substructure values, interior dofs keep their (unique) value."""
+        substructure values, interior dofs keep their (unique) value.
+
+        Pinned by test_oracle_levels.py::test_averaging_is_projection_onto_U (E U = U, E^2 = E).
+        """
         u = np.zeros(self.n)
         for sb, zs in zip(self.subs, z):
             u[sb.idofs] = zs[:sb.n_i]
@@ -280,6 +307,8 @@ class Level:
         return u
 
     def average_transpose(self, r: np.ndarray) -> List[np.ndarray]:
+        """E^T.  Pinned by test_oracle_solver.py::test_spectrum_at_least_one (a wrong transpose
+        breaks symmetry and the lower bound 1)."""
         out = []
         for sb in self.subs:
             g = np.empty(sb.dofs.size)
@@ -292,6 +321,7 @@ class Level:
 # -------------------------------------------------------------------- builders
 
 def level_one(prob, initial="ce") -> Level:
+    """Pinned by test_oracle_levels.py::test_classification_counts_2x2x2."""
     fmap, free = fe.free_dof_map(prob)
     d = prob.dofs_per_node
     ed = fmap[fe.element_dofs(prob)]
@@ -314,7 +344,12 @@ def level_one(prob, initial="ce") -> Level:
 
 def level_next(prev: Level, parent: np.ndarray, n_subs: int, cuts, initial="ce") -> Level:
     """Level i+1: elements are level-i substructures with matrices Psi^T S Psi,
-    dofs are level-i coarse dofs; level-(i+1) nodes are level-i coarse objects."""
+    dofs are level-i coarse dofs; level-(i+1) nodes are level-i coarse objects.
+
+    Pinned by test_oracle_solver.py::test_three_levels_single_top_sub_equals_two_levels,
+    test_three_levels_spectrum and
+    test_oracle_levels.py::test_box_vertex_corners_ragged_and_level_two (level-2 corners).
+    """
     node_of_dof = np.empty(prev.n_coarse, dtype=np.int64)
     comp_of_dof = np.empty(prev.n_coarse, dtype=np.int64)
     eligible, vertex, coords = [], [], []

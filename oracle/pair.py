@@ -48,7 +48,10 @@ class PairResult:
 
 
 def _factor_space_eig(a, b):
-    """Eigenpairs of a w = lambda b w on the complement of null(b), descending."""
+    """Eigenpairs of a w = lambda b w on the complement of null(b), descending.
+
+    Pinned by test_oracle_pair.py::test_literal_equals_reduced.
+    """
     sig, v = np.linalg.eigh(0.5 * (b + b.T))
     keep = sig > DROP * max(sig.max(), 0.0)
     t = v[:, keep] / np.sqrt(sig[keep])
@@ -59,6 +62,8 @@ def _factor_space_eig(a, b):
 
 
 def shared_info(lev, s, t):
+    """Index bookkeeping of the shared dofs.  Pinned by
+    test_oracle_pair.py::test_all_shared_dofs_corners_gives_zero."""
     key = (min(s, t), max(s, t))
     sbs, sbt = lev.subs[s], lev.subs[t]
     f = np.intersect1d(sbs.gdofs, sbt.gdofs)
@@ -77,7 +82,11 @@ def shared_info(lev, s, t):
 
 
 def literal(lev, s, t):
-    """Dense eq. eig-matrix on Gamma^s + Gamma^t.  Returns (lam, W, A, info)."""
+    """Dense eq. eig-matrix on Gamma^s + Gamma^t.  Returns (lam, W, A, info).
+
+    Pinned by test_oracle_pair.py::test_literal_equals_reduced (two independent formulations agree)
+    and test_all_shared_dofs_corners_gives_zero.
+    """
     info = shared_info(lev, s, t)
     sbs, sbt = lev.subs[s], lev.subs[t]
     ns, nt = sbs.n_g, sbt.n_g
@@ -102,6 +111,7 @@ def literal(lev, s, t):
 
 
 def _schur_onto(smat, keep_pos):
+    """Pinned by test_oracle_pair.py::test_literal_equals_reduced."""
     n = smat.shape[0]
     other = np.setdiff1d(np.arange(n), keep_pos)
     sff = smat[np.ix_(keep_pos, keep_pos)]
@@ -113,6 +123,7 @@ def _schur_onto(smat, keep_pos):
 
 
 def _pinv_psd(m):
+    """Pinned by test_oracle_pair.py::test_literal_equals_reduced."""
     sig, v = np.linalg.eigh(0.5 * (m + m.T))
     keep = sig > DROP * max(sig.max(), 0.0)
     return (v[:, keep] / sig[keep]) @ v[:, keep].T
@@ -121,7 +132,10 @@ def _pinv_psd(m):
 def reduced(lev, s, t):
     """Same positive eigenvalues as `literal`, from the jump on the shared dofs.
     Returns (lam, J, N, info) with J the jumps (columns) of the eigenvectors,
-    normalized so that j^T H j = 1."""
+    normalized so that j^T H j = 1.
+
+    Pinned by test_oracle_pair.py::test_literal_equals_reduced.
+    """
     info = shared_info(lev, s, t)
     sbs, sbt = lev.subs[s], lev.subs[t]
     ps, pt, ds, dt = info["ps"], info["pt"], info["ds"], info["dt"]
@@ -138,7 +152,10 @@ def reduced(lev, s, t):
 
 
 def rows_from_reduced(nmat, jumps, info):
-    """c^s on f: P_C N j, with P_C the orthogonal projector onto null(C_f)."""
+    """c^s on f: P_C N j, with P_C the orthogonal projector onto null(C_f).
+
+    Pinned by test_oracle_pair.py::test_prop1_sign_structure and test_corollary1_added_rows.
+    """
     c = nmat @ jumps
     cf = info["cf"]
     if cf.shape[0]:
@@ -147,7 +164,10 @@ def rows_from_reduced(nmat, jumps, info):
 
 
 def face_rows(crows_f, info, lev):
-    """Drop entries off the face-class dofs, orthonormalize (reduced QR)."""
+    """Drop entries off the face-class dofs, orthonormalize (reduced QR).
+
+    Pinned by test_oracle_pair.py::test_corollary1_added_rows.
+    """
     f = info["f"]
     face_dofs = info["face_dofs"]
     sel = np.isin(f, face_dofs)
@@ -162,6 +182,8 @@ def face_rows(crows_f, info, lev):
 
 
 def solve_pair(lev, s, t, tau, max_per_face=10, form="reduced") -> PairResult:
+    """Pinned by test_oracle_pair.py::test_corollary1_added_rows (after the k rows the pair maximum
+    is lambda_{k+1})."""
     if form == "literal":
         lam, w, amat, info = literal(lev, s, t)
         pos = lam > 0
@@ -181,5 +203,8 @@ def solve_pair(lev, s, t, tau, max_per_face=10, form="reduced") -> PairResult:
 
 
 def pairs_of(lev) -> List[tuple]:
-    """Every pair sharing at least one face-class dof."""
+    """Every pair sharing at least one face-class dof.
+
+    Pinned by test_oracle_levels.py::test_classification_counts_2x2x2 (12 faces).
+    """
     return sorted(k for k, nodes in lev.faces.items() if nodes.size)

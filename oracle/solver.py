@@ -44,6 +44,8 @@ class LevelReport:
 class Hierarchy:
     def __init__(self, prob, levels=None, tau=None, initial="ce", adaptive=True,
                  max_per_face=10, form="reduced", timers=None):
+        """Algorithm 3.  Pinned by test_oracle_solver.py::test_solution_vs_direct,
+        test_spectrum_at_least_one and test_three_levels_spectrum."""
         self.prob = prob
         self.nlev = prob.levels if levels is None else levels
         self.tau = prob.tau if tau is None else tau
@@ -84,9 +86,12 @@ class Hierarchy:
         self._tick("coarse", t0)
 
     def _tick(self, key, t0):
+        """Timing bookkeeping only."""
         self.timers[key] = self.timers.get(key, 0.0) + time.perf_counter() - t0
 
     def _adapt(self, lev, max_per_face, form) -> LevelReport:
+        """Pinned by test_oracle_solver.py::test_spectrum_at_least_one (adaptive) and
+        test_oracle_pair.py::test_corollary1_added_rows."""
         pairs = pr.pairs_of(lev)
         lams, nsel, after = [], [], []
         results = []
@@ -107,6 +112,9 @@ class Hierarchy:
 
     # ------------------------------------------------------------ Algorithm 1
     def apply(self, r: np.ndarray, i: int = 0) -> np.ndarray:
+        """Algorithm 1.  Pinned by test_oracle_solver.py::test_spectrum_at_least_one (spectrum of M
+        A >= 1), test_all_corners_one_iteration and
+        test_three_levels_single_top_sub_equals_two_levels."""
         lev, a = self.levels[i], self.ops[i]
         u_i = np.zeros(lev.n)
         for sb in lev.subs:
@@ -134,6 +142,7 @@ class Hierarchy:
         return u_i + u_b - v_i                                                 # eq. ML-ui
 
     def report(self):
+        """Bookkeeping only (no arithmetic)."""
         return self.reports
 
 
@@ -149,6 +158,7 @@ class PCGResult:
 
 
 def lanczos_cond(alphas, betas) -> float:
+    """Pinned by test_oracle_solver.py::test_lanczos_condition_estimate."""
     k = len(alphas)
     if k == 0:
         return 1.0
@@ -163,6 +173,7 @@ def lanczos_cond(alphas, betas) -> float:
 
 
 def pcg(a, f, precond, rtol=1e-8, maxit=1000) -> PCGResult:
+    """Pinned by test_oracle_solver.py::test_solution_vs_direct."""
     u = np.zeros_like(f)
     r = f.copy()
     nf = np.linalg.norm(f)
@@ -196,7 +207,10 @@ def pcg(a, f, precond, rtol=1e-8, maxit=1000) -> PCGResult:
 
 
 def solve(prob, rtol=1e-8, **kw):
-    """Set-up + PCG on the level-1 problem; returns (hierarchy, PCGResult, f)."""
+    """Set-up + PCG on the level-1 problem; returns (hierarchy, PCGResult, f).
+
+    Pinned by test_oracle_solver.py::test_solution_vs_direct.
+    """
     h = Hierarchy(prob, **kw)
     f = fe.load_vector(prob)
     t0 = time.perf_counter()

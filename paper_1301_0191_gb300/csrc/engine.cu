@@ -21,6 +21,7 @@
 #include <map>
 
 #include "engine_impl.h"
+#include "tc_gemm.h"
 
 namespace amb {
 
@@ -673,15 +674,28 @@ void Engine<T>::schur_apply(int level, int width, const void* x, void* y) {
     fl += 2.0 * ng * ng * width;
     by += (double)ng * ng * sizeof(T) + 2.0 * ng * width * sizeof(T);
   }
+  bool tc = false;
   if (width == 1) {
     std::vector<GemvDesc> g;
     for (auto& q : d) g.push_back(GemvDesc{q.m, q.k, q.lda, 0, q.a, q.b, q.c});
     gemv_batched<T>(st, ring, g, 0, T(1), T(0), dptr<T>(L.S), static_cast<const T*>(x), static_cast<T*>(y));
+  } else if constexpr (std::is_same<T, float>::value) {
+    if (width >= kTcSchurWidth) {
+      // FP32 form, wide blocks: tensor cores (3xTF32); Y(i, j) = sum_k S(i, k) X(k, j), X read K-major
+      std::vector<TcGemm> t;
+      for (auto& q : d) t.push_back(TcGemm{q.a, q.b, q.c, q.lda, q.ldb, q.ldc, q.m, q.n, q.k, 0, 1, 0});
+      tc_gemm(st, ring, t, 1.f, 0.f, dptr<float>(L.S), static_cast<const float*>(x), static_cast<float*>(y),
+              dptr<int>(status));
+      tc = true;
+    } else {
+      gemm_batched<T>(st, ring, d, 0, T(1), T(0), dptr<T>(L.S), static_cast<const T*>(x), static_cast<T*>(y));
+    }
   } else {
     gemm_batched<T>(st, ring, d, 0, T(1), T(0), dptr<T>(L.S), static_cast<const T*>(x), static_cast<T*>(y));
   }
   tm.fam_flops[AMB_FAM_SCHUR] += fl;
   tm.fam_bytes[AMB_FAM_SCHUR] += by;
+  if (tc) check_status("Schur apply on the tensor cores", AMB_ETIMEOUT);
 }
 
 template <typename T>

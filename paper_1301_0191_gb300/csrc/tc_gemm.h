@@ -8,6 +8,7 @@
 namespace amb {
 
 constexpr int kTcKMax = 256;   // widest K of one trailing update (the outer Cholesky block)
+constexpr int kTcSchurWidth = 64;  // FP32 Schur applies of at least this many columns use the tensor cores
 
 // One trailing update C(lower) -= P P^T of a substructure matrix: P is rem x
 // k at element offset p (column-major, ld), C is rem x rem at offset c.

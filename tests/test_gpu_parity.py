@@ -252,6 +252,34 @@ def test_schur_apply(B):
     ctx.close()
 
 
+def test_schur_apply_fp32_tensor_cores(B):
+    """FP32 form, widths 64 and 100 (tensor cores, 3xTF32, K in chunks of 256):
+    Y = S X against the FP64 product of the exported FP32 S with the same X,
+    within the 3xTF32 accumulation error (64 units of 2^-24 relative to sum |S||X|;
+    the measured rms is a few units)."""
+    import torch
+    prob = ai.toy(6, 3, 19, split=(2, 2, 1))   # n_G up to ~500: two K chunks
+    ctx = _ctx(B, prob, adaptive=0, precision=B.FP32)
+    n = ctx.level_info(1).n_subs
+    sizes = [int(ctx.export(B.X_SUB_SIZES, 1, s, np.int32)[1]) for s in range(n)]
+    assert max(sizes) > 256
+    gen = torch.Generator(device="cuda").manual_seed(9)
+    for width in (64, 100):
+        x = torch.randn(sum(sizes) * width, dtype=torch.float32, device="cuda", generator=gen)
+        y = torch.empty_like(x)
+        ctx.schur_apply(1, width, x, y)
+        xh, yh = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+        o = 0
+        for s, ng in enumerate(sizes):
+            S = ctx.export(B.X_SCHUR, 1, s, np.float64).reshape(ng, ng, order="F")   # the FP32 S, exported as FP64
+            X = xh[o:o + ng * width].reshape(ng, width, order="F")
+            Y = yh[o:o + ng * width].reshape(ng, width, order="F")
+            bound = 64 * 2.0 ** -24 * (np.abs(S) @ np.abs(X)) + 1e-30
+            assert np.all(np.abs(Y - S @ X) <= bound), (width, s)
+            o += ng * width
+    ctx.close()
+
+
 def test_host_made_failures(B):
     prob = ai.toy(3, 1, 18, split=(2, 1, 1))
     bad = prob.coeff.copy()
