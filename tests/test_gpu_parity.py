@@ -217,6 +217,33 @@ def test_fp32_preconditioner_reaches_fp64_tolerance(B):
     c32.close()
 
 
+def test_fp32_form_three_levels(B):
+    """FP32 form on three levels (elasticity, 4x2x1 substructures in two
+    level-2 groups): PCG reaches the FP64 tolerance, the solution matches the
+    sparse direct solve to 1e-6, and the selections per face match the FP64
+    form within +-1 on both levels."""
+    groups = [np.array([0, 2, 4]), np.array([0, 2]), np.array([0, 1])]
+    prob = ai.toy(3, 3, 41, split=(4, 2, 1), levels=3, groups=groups, sigma=1.0, tau=2.0)
+    c64 = _ctx(B, prob, lobpcg_tol=1e-8, lobpcg_maxit=300)
+    c32 = _ctx(B, prob, precision=B.FP32, lobpcg_tol=1e-6, lobpcg_maxit=300)
+    f = c64.load_vector(prob.body)
+    u64, i64 = c64.solve(f)
+    u32, i32 = c32.solve(f)
+    r64, r32 = c64.report(), c32.report()
+    c64.close()
+    c32.close()
+    assert i32.rel_residual <= 1e-8 and i32.true_rel_residual <= 1e-7
+    free = _free(prob)
+    h, res, f_free = solver.solve(prob)
+    ud = spla.spsolve(h.ops[0].tocsc(), f_free)
+    assert np.linalg.norm(u32[free] - ud) <= 1e-6 * np.linalg.norm(ud)
+    assert i32.iterations <= i64.iterations + 3
+    sel64 = {(p["level"], p["s"], p["t"]): p["n_selected"] for p in r64["pairs"]}
+    sel32 = {(p["level"], p["s"], p["t"]): p["n_selected"] for p in r32["pairs"]}
+    assert sel64.keys() == sel32.keys()
+    assert all(abs(sel64[k] - sel32[k]) <= 1 for k in sel64)
+
+
 def test_compliance_gradient(B):
     prob = ai.toy(3, 1, 16, split=(2, 2, 1), sigma=1.0)
     ctx = _ctx(B, prob)
