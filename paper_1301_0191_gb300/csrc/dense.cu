@@ -205,8 +205,12 @@ k_gemm(GemmArgs<T, TA> g) {
 // b_hi + b_lo, both FP32) goes into lo.  The result hi + lo has about 44
 // significant bits, enough for the FP64-consistent Rayleigh-Ritz of the
 // pair eigenproblems; plain FP32 accumulation is not (see lobpcg.cu).
+// Tiles with at most 8 outputs per thread are held to 64 registers (1024
+// resident threads per SM): the TwoSum chains are dependent, so the kernel
+// needs warps to hide their latency (96 registers left 20 warps per SM and
+// the FMA pipe half idle).  The 16-output tile would spill at 64.
 template <int BM, int BN, int BK, int TM, int TN>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+__global__ void __launch_bounds__((BM / TM) * (BN / TN), TM * TN <= 8 ? 1024 / ((BM / TM) * (BN / TN)) : 1)
 k_gemm_df(GemmArgs<double, float> g) {
   constexpr int NTX = BM / TM, NTY = BN / TN, NT = NTX * NTY;
   constexpr int LA = BM * BK / NT, LB = BK * BN / NT;

@@ -1299,6 +1299,17 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     applyB(1, 7);
     rayleigh_ritz(it == 0 ? 2 * m : 3 * m);
   }
+  // consistency refresh: A X and B X are carried by the same coefficient
+  // recurrence as X, and with a near-dependent [X W P] the coefficients are
+  // large enough for them to drift from the products of the current X.
+  // Recompute both for every pair and finish with Rayleigh-Ritz on X alone,
+  // so that the reported eigenvalues are Rayleigh quotients of the vectors
+  // and the rows below come from fresh A X.
+  std::fill(active.begin(), active.end(), 1);
+  AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+  applyA(0, 3);
+  applyB(0, 6);
+  rayleigh_ritz(m);
   check();
   // ------------------------------------------------ selection and rows
   std::vector<int> nsel(np, 0);
