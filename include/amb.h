@@ -120,7 +120,9 @@ typedef struct {
   int32_t n_rows;               /* rows kept after QR */
   int32_t converged;            /* 1 if every residual met lobpcg_tol */
   int32_t iterations;           /* LOBPCG iterations */
-  double lambda[AMB_MAX_EIG];   /* computed eigenvalues, descending */
+  double lambda[AMB_MAX_EIG];   /* computed eigenvalues, descending; where the pair space has fewer
+                                   than n_computed directions of non-negligible B-norm, the
+                                   columns beyond them report 0 */
   double residual;              /* max over the used columns (selected + next) of
                                    ||A x - lam B x|| / (max(lam, tau/10) ||B x||) */
 } amb_pair_report;

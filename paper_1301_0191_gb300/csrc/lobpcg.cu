@@ -1237,13 +1237,21 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const double tol = cfg.opt.lobpcg_tol;
   const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
   const double tau = cfg.tau;
-  std::vector<double> resid(np, 0.0), best(np, 1e300);
+  std::vector<double> resid(np, 0.0), best(np, 1e300), prev((size_t)np * m, -1e300);
   std::vector<int> since(np, 0);
   // stagnation: far from tol, kStall iterations without halving the worst
   // used residual; within kFloor x tol (the residual floor of the operator
-  // products, reached by some pairs of the FP32 form), kFloorStall
+  // products, reached by some pairs of the FP32 form), kFloorStall.
+  // FP64 form: a used Ritz value that still rises by more than tol (relative)
+  // also counts as progress.  The columns of very large eigenvalues (a stiff
+  // inclusion across the face, lambda ~ 1e5 tau) have a residual floor far
+  // above tol, because B w is tiny against B's norm there, while their Ritz
+  // values still converge; without this rule such a pair stops with its top
+  // eigenvalue a few 1e-4 low.  Ritz values of the FP32 form carry the FP32
+  // pencil's noise, so that form keeps the residual rule alone.
   constexpr int kStall = 20, kFloorStall = 3;
   constexpr double kFloor = 10.0;
+  constexpr bool kRitzProgress = sizeof(T) == sizeof(double);
   auto check = [&]() {
     k_lob_resid<V><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();
@@ -1261,9 +1269,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       while (kuse < m && kuse < maxad && hl[(size_t)p * m + kuse] > tau) ++kuse;
       kuse = std::min(m, kuse + 1);
       double worst = 0.0;
+      bool rising = false;
       for (int k = 0; k < kuse; ++k) {
         const double l = hl[(size_t)p * m + k];
         const double b = hb[(size_t)p * m + k];
+        if (kRitzProgress && l - prev[(size_t)p * m + k] > tol * std::max(std::fabs(l), lref)) rising = true;
         if (b == 0.0) continue;   // dropped direction (rank-deficient pair space)
         const double ratio = hr[(size_t)p * m + k] / (std::max(std::fabs(l), lref) * b);
         worst = std::max(worst, std::isfinite(ratio) ? ratio : 1e300);
@@ -1273,8 +1283,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       conv[p] = ok ? 1 : 0;
       // a stagnating pair stops iterating (reported as not converged, with
       // its residual)
+      for (int k = 0; k < m; ++k) prev[(size_t)p * m + k] = hl[(size_t)p * m + k];
       if (worst < 0.5 * best[p]) {
         best[p] = worst;
+        since[p] = 0;
+      } else if (rising) {
         since[p] = 0;
       } else {
         ++since[p];

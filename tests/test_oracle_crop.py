@@ -1,0 +1,61 @@
+"""The crop of tests/crops.py reproduces the whole-mesh oracle on one face:
+S^s, S^t and the pair eigenvalues and selection of that face, on irregular
+box partitions with high-contrast slabs (scalar) and log-normal elasticity,
+for interior faces and faces on the Dirichlet boundary.  This pins the
+locality that the full-size GPU checks of the 96^3 workload rely on."""
+import numpy as np
+import pytest
+
+import amb_inputs as ai
+from crops import crop_around
+from oracle import fe, levels as olv, pair as opr
+
+
+def _irregular(n, parts, lo, hi, dpn, seed):
+    rng = np.random.default_rng(np.random.PCG64(seed))
+    cuts1 = [ai.irregular_cuts(n, parts, lo, hi, rng) for _ in range(3)]
+    if dpn == 1:
+        coeff = ai.slabs(n, rng, 1.0e6, 0.10)
+    else:
+        coeff = np.exp(1.5 * rng.standard_normal(n ** 3))
+    return ai._make(f"crop{dpn}", n, parts, dpn, coeff, 2, 2.0, cuts1=cuts1)
+
+
+@pytest.mark.parametrize("dpn,n,parts,lo,hi,seed", [(1, 20, 4, 3, 7, 5), (3, 13, 4, 3, 4, 6)])
+def test_crop_matches_whole_mesh(dpn, n, parts, lo, hi, seed):
+    prob = _irregular(n, parts, lo, hi, dpn, seed)
+    full = olv.level_one(prob)
+    full.schur()
+    pairs = opr.pairs_of(full)
+    # an interior face, a face on the Dirichlet plane x = 0 and the last face
+    interior = [(s, t) for s, t in pairs
+                if all(0 < b < parts - 1 for b in ai_box(prob, s) + ai_box(prob, t))]
+    on_x0 = [(s, t) for s, t in pairs if ai_box(prob, s)[0] == 0 and ai_box(prob, t)[0] == 0]
+    picks = [interior[0], on_x0[len(on_x0) // 2], pairs[-1]]
+    free = fe.free_dof_map(prob)[1]      # free index -> full-mesh dof id
+    nsel = 0
+    for s, t in picks:
+        crop, sub_map, dof_map = crop_around(prob, s, t)
+        inv = {v: k for k, v in sub_map.items()}
+        lev = olv.level_one(crop)
+        lev.schur()
+        for sub in (s, t):
+            sb, sf = lev.subs[inv[sub]], full.subs[sub]
+            # same dofs in the same class order (interior, then interface)
+            assert np.array_equal(np.sort(dof_map[sb.idofs]), np.sort(free[sf.idofs]))
+            pos = {int(d): i for i, d in enumerate(dof_map[sb.gdofs])}
+            perm = np.array([pos[int(d)] for d in free[sf.gdofs]])
+            assert np.abs(sb.s[np.ix_(perm, perm)] - sf.s).max() <= 1e-12 * np.abs(sf.s).max()
+        rf = opr.solve_pair(full, s, t, prob.tau)
+        cs, ct = inv[s], inv[t]
+        rc = opr.solve_pair(lev, min(cs, ct), max(cs, ct), prob.tau)
+        assert rc.n_selected == rf.n_selected
+        assert len(rc.lam) == len(rf.lam)
+        assert np.allclose(rc.lam, rf.lam, rtol=1e-9, atol=0.0)
+        nsel += rf.n_selected
+    assert nsel > 0          # the picks exercise the selection, not only lambda <= tau
+
+
+def ai_box(prob, s):
+    na, nb = (len(c) - 1 for c in prob.cuts[0][:2])
+    return (s % na, (s // na) % nb, s // (na * nb))
