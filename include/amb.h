@@ -175,6 +175,9 @@ void amb_default_options(amb_options* o);
  * bddc_pair), add the adaptive rows (eq. d-def, Sec. 7.2) and set up the
  * coarse bases (eq. local_saddle_point_problem) and the top coarse
  * factorization.  levels >= 2; tau > 0 is the per-level target.
+ * The decomposition is checked on the host before any device work:
+ * AMB_EINVAL if an element or parent index is out of range, a substructure
+ * of some level is empty, or is not a box of elements.
  * *out receives a new context even on failure (NULL only on AMB_ENOMEM),
  * so that amb_last_error can explain; release it with amb_destroy. */
 int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs,

@@ -156,6 +156,20 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
     AMB_CHECK(mesh->dirichlet_node_mask && part->elem_to_sub && coeffs->coeff, AMB_EINVAL, "NULL array");
     AMB_CHECK(mesh->dofs_per_node == 1 || (coeffs->poisson_ratio > -1.0 && coeffs->poisson_ratio < 0.5), AMB_EINVAL,
               "poisson_ratio out of range");
+    // the decomposition hierarchy is checked on the host before any device work
+    AMB_CHECK(!is_device(mesh->dirichlet_node_mask) && !is_device(part->elem_to_sub), AMB_EINVAL,
+              "dirichlet_node_mask and the partition must be host arrays");
+    AMB_CHECK(part->n_sub1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
+    c->cfg.nsubs.push_back(part->n_sub1);
+    for (int i = 0; i < levels - 2; ++i) {
+      AMB_CHECK(part->sub_to_parent && part->n_sub && part->sub_to_parent[i], AMB_EINVAL,
+                "sub_to_parent required for levels > 2");
+      AMB_CHECK(!is_device(part->sub_to_parent[i]), AMB_EINVAL, "sub_to_parent must be host arrays");
+      const int nprev = c->cfg.nsubs.back();
+      c->cfg.parents.emplace_back(part->sub_to_parent[i], part->sub_to_parent[i] + nprev);
+      c->cfg.nsubs.push_back(part->n_sub[i]);
+    }
+    validate_partition(mesh->nx, mesh->ny, mesh->nz, part->elem_to_sub, c->cfg.parents, c->cfg.nsubs);
     c->opt = *opt;
     c->st = static_cast<cudaStream_t>(opt->cuda_stream);
     alloc_stream() = c->st;
@@ -170,8 +184,6 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
     m.nel = (int64_t)m.nx * m.ny * m.nz;
     m.nnodes = (int64_t)(m.nx + 1) * (m.ny + 1) * (m.nz + 1);
     m.ndof = m.nnodes * m.dpn;
-    AMB_CHECK(!is_device(mesh->dirichlet_node_mask) && !is_device(part->elem_to_sub), AMB_EINVAL,
-              "dirichlet_node_mask and the partition must be host arrays");
     m.dir_h.assign(mesh->dirichlet_node_mask, mesh->dirichlet_node_mask + m.nnodes);
     m.elem_sub_h.assign(part->elem_to_sub, part->elem_to_sub + m.nel);
     c->ring.init(64 << 20);
@@ -189,15 +201,6 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
     c->cfg.opt = *opt;
     c->cfg.levels = levels;
     c->cfg.tau = tau;
-    AMB_CHECK(part->n_sub1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
-    c->cfg.nsubs.push_back(part->n_sub1);
-    for (int i = 0; i < levels - 2; ++i) {
-      AMB_CHECK(part->sub_to_parent && part->n_sub && part->sub_to_parent[i], AMB_EINVAL,
-                "sub_to_parent required for levels > 2");
-      const int nprev = c->cfg.nsubs.back();
-      c->cfg.parents.emplace_back(part->sub_to_parent[i], part->sub_to_parent[i] + nprev);
-      c->cfg.nsubs.push_back(part->n_sub[i]);
-    }
     alloc_vectors(c);
     cudaEvent_t e0, e1;
     AMB_CUDA(cudaEventCreate(&e0));

@@ -359,6 +359,64 @@ void add_adaptive_rows(LevelTopo& L, int pi, const std::vector<std::vector<doubl
   }
 }
 
+// ------------------------------------------------------------------ checks
+
+void validate_partition(int nx, int ny, int nz, const int32_t* elem_to_sub,
+                        const std::vector<std::vector<int32_t>>& parents, const std::vector<int>& nsubs) {
+  struct Box {
+    int64_t lo[3] = {INT64_MAX, INT64_MAX, INT64_MAX}, hi[3] = {-1, -1, -1};
+    int64_t count = 0;
+    void add(const Box& b) {
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = std::min(lo[a], b.lo[a]);
+        hi[a] = std::max(hi[a], b.hi[a]);
+      }
+      count += b.count;
+    }
+    int64_t volume() const { return (hi[0] - lo[0] + 1) * (hi[1] - lo[1] + 1) * (hi[2] - lo[2] + 1); }
+  };
+  auto check_boxes = [](const std::vector<Box>& boxes, int level) {
+    for (size_t s = 0; s < boxes.size(); ++s) {
+      AMB_CHECK(boxes[s].count > 0, AMB_EINVAL,
+                "level-" + std::to_string(level) + " substructure " + std::to_string(s) + " is empty");
+      AMB_CHECK(boxes[s].count == boxes[s].volume(), AMB_EINVAL,
+                "level-" + std::to_string(level) + " substructure " + std::to_string(s) +
+                    " is not a box of elements");
+    }
+  };
+  const int n1 = nsubs.empty() ? 0 : nsubs[0];
+  AMB_CHECK(n1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
+  std::vector<Box> boxes(n1);
+  int64_t e = 0;
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i, ++e) {
+        const int32_t s = elem_to_sub[e];
+        AMB_CHECK(s >= 0 && s < n1, AMB_EINVAL, "elem_to_sub out of range");
+        Box& b = boxes[s];
+        const int64_t x[3] = {i, j, k};
+        for (int a = 0; a < 3; ++a) {
+          b.lo[a] = std::min(b.lo[a], x[a]);
+          b.hi[a] = std::max(b.hi[a], x[a]);
+        }
+        ++b.count;
+      }
+  check_boxes(boxes, 1);
+  for (size_t l = 0; l < parents.size(); ++l) {
+    const int nn = nsubs[l + 1];
+    AMB_CHECK(nn >= 1, AMB_EINVAL, "every level needs at least one substructure");
+    AMB_CHECK(parents[l].size() == boxes.size(), AMB_EINVAL, "sub_to_parent has the wrong length");
+    std::vector<Box> up(nn);
+    for (size_t s = 0; s < boxes.size(); ++s) {
+      const int32_t q = parents[l][s];
+      AMB_CHECK(q >= 0 && q < nn, AMB_EINVAL, "sub_to_parent out of range");
+      up[q].add(boxes[s]);
+    }
+    check_boxes(up, (int)l + 2);
+    boxes.swap(up);
+  }
+}
+
 // ------------------------------------------------------------------ level 1
 
 LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirichlet, const int32_t* elem_to_sub,

@@ -79,6 +79,15 @@ struct LevelTopo {
   std::vector<int> node_tags_of_obj;          // per object: common boundary bits
 };
 
+// Checks the decomposition hierarchy before anything is built: element and
+// parent indices in range, no empty substructure, and every substructure of
+// every level a box of elements (the box-vertex corner rule and the edge
+// classes assume box partitions, Sec. 2 and 7.1).  parents[i] maps level-(i+1)
+// substructures to level-(i+2) ones; nsubs[i] = substructures on level i+1.
+// Throws Error(AMB_EINVAL) naming the first violation.  Host arrays only.
+void validate_partition(int nx, int ny, int nz, const int32_t* elem_to_sub,
+                        const std::vector<std::vector<int32_t>>& parents, const std::vector<int>& nsubs);
+
 // Level 1 from the mesh.  dirichlet: per node; elem_to_sub: per element.
 LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirichlet, const int32_t* elem_to_sub,
                           int n_subs, int initial, std::vector<int32_t>& elem_local /* n_el * 8*dpn */);

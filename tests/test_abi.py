@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -48,3 +49,37 @@ def test_kernel_stats_fields_follow_the_header():
     names = re.findall(r"(?:double|int64_t)\s+([a-z_]+)", body)
     assert names == [f[0] for f in B.KernelStats._fields_]
     assert ctypes.sizeof(B.KernelStats) == 8 * (4 * B.FAM_N + 8 + 4)
+
+
+def _mesh_2x2(nx=4):
+    mask = np.zeros((3, 3, nx + 1), dtype=np.uint8)
+    mask[:, :, 0] = 1                      # x = 0 fixed
+    return dict(nx=nx, ny=2, nz=2, h=1.0 / nx, dofs_per_node=1, dirichlet_node_mask=mask.ravel(),
+                coeff=np.ones(nx * 4), poisson_ratio=0.3, tau=10.0)
+
+
+@pytest.mark.parametrize("case", ["out_of_range", "not_a_box", "empty", "parent_not_a_box", "parent_out_of_range"])
+def test_setup_rejects_invalid_partitions(case):
+    """The decomposition is checked on the host before any device work:
+    AMB_EINVAL with the violation named (no GPU needed)."""
+    from paper_1301_0191_gb300 import binding as B
+    m = _mesh_2x2()
+    i = np.tile(np.arange(4), 4)                         # element (i, j, k) -> e = i + 4 (j + 2 k)
+    e2s, n1, levels, parents, nsub, words = (i >= 2).astype(np.int32), 2, 2, (), (), ""
+    if case == "out_of_range":
+        e2s[5], words = 2, "out of range"
+    elif case == "not_a_box":
+        e2s[2], words = 0, "not a box"                   # element (2, 0, 0) joins the x < 2 box
+    elif case == "empty":
+        n1, words = 3, "substructure 2 is empty"
+    elif case == "parent_not_a_box":
+        e2s, n1, levels, parents, nsub = i.astype(np.int32), 4, 3, [np.array([0, 1, 0, 1])], [2]
+        words = "level-2 substructure 0 is not a box"
+    else:
+        e2s, n1, levels, parents, nsub = i.astype(np.int32), 4, 3, [np.array([0, 0, 1, 2])], [2]
+        words = "sub_to_parent out of range"
+    with pytest.raises(B.AmbError) as ei:
+        B.Context(m["nx"], m["ny"], m["nz"], m["h"], 1, m["dirichlet_node_mask"], m["coeff"], 0.3, e2s, n1,
+                  levels, m["tau"], parents, nsub)
+    assert ei.value.status == B.EINVAL
+    assert words in str(ei.value)
