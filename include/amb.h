@@ -247,6 +247,21 @@ typedef struct {
 } amb_level_sizes;
 int amb_level_info(const amb_ctx* ctx, int32_t level, amb_level_sizes* info);
 
+/* Host-only plan of level 1, without a context and without any device work:
+ * the classification of Sec. 2 (interface, faces, edges, box-vertex
+ * corners) and the initial constraints of Sec. 7.1, for sizing a run
+ * before amb_setup (device memory grows with sum n_I^2 and schur_words).
+ * info receives what amb_level_info(ctx, 1, ...) reports for the same input
+ * before adaptivity: n_coarse counts the initial coarse dofs only.
+ * sub_sizes: NULL, or [host] 4 * n_sub1 int32 receiving per substructure
+ * (n_I, n_Gamma, corner dofs, initial coarse dofs).  mesh, part: as for
+ * amb_setup; only dofs_per_node, the sizes, the Dirichlet mask and
+ * elem_to_sub are read (coefficients are not needed).  Errors: AMB_EINVAL
+ * for NULL arguments, an unknown initial_constraints or a partition that
+ * amb_setup would reject. */
+int amb_plan_level1(const amb_mesh* mesh, const amb_partition* part, int32_t initial_constraints,
+                    amb_level_sizes* info, int32_t* sub_sizes);
+
 /* Export internal results for verification.  Two-call size query as in
  * amb_eigen_report.  `what`:
  *  AMB_X_SUB_DOFS   int64: dofs of substructure `index`, [interior...,

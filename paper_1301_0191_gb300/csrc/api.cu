@@ -376,38 +376,79 @@ int amb_schur_apply(amb_ctx* c, int32_t level, int32_t width, const void* x, voi
   });
 }
 
+namespace {
+// sizes of one level; n_dofs is passed in (level 1: free dofs of the mesh)
+void fill_sizes(const amb::LevelTopo& tp, int64_t n_dofs, amb_level_sizes* info) {
+  memset(info, 0, sizeof(*info));
+  info->n_subs = tp.n_subs;
+  info->n_pairs = (int32_t)tp.pairs.size();
+  info->n_corner_nodes = tp.n_corner_nodes;
+  info->n_edges = tp.n_edges;
+  info->n_faces = tp.n_faces;
+  info->n_dofs = n_dofs;
+  info->n_coarse = tp.n_coarse;
+  for (const auto& sb : tp.subs) {
+    const double ni = sb.n_i, ng = sb.n_g, ndl = sb.n_d();
+    info->sum_ni += sb.n_i;
+    info->sum_ngamma += sb.n_g;
+    info->max_ni = std::max<int64_t>(info->max_ni, sb.n_i);
+    info->max_ngamma = std::max<int64_t>(info->max_ngamma, sb.n_g);
+    info->max_ndelta = std::max<int64_t>(info->max_ndelta, sb.n_d());
+    info->factor_flops += ni * ni * ni / 3.0 + ni * ni * ng + ni * ng * ng + ndl * ndl * ndl / 3.0;
+    info->schur_words += ng * ng;
+  }
+}
+
+int64_t free_dofs(const uint8_t* dir, int64_t nnodes, int dpn) {
+  int64_t nd = 0;
+  for (int64_t i = 0; i < nnodes; ++i) nd += dir[i] ? 0 : 1;
+  return nd * dpn;
+}
+}  // namespace
+
 int amb_level_info(const amb_ctx* cc, int32_t level, amb_level_sizes* info) {
   amb_ctx* c = const_cast<amb_ctx*>(cc);
   return guarded(c, [&]() {
     AMB_CHECK(c->eng && info, AMB_EINVAL, "no set-up or NULL info");
     AMB_CHECK(level >= 1 && level <= c->eng->n_levels(), AMB_EINVAL, "level out of range");
     const LevelTopo& tp = c->eng->topo(level);
-    memset(info, 0, sizeof(*info));
-    info->n_subs = tp.n_subs;
-    info->n_pairs = (int32_t)tp.pairs.size();
-    info->n_corner_nodes = tp.n_corner_nodes;
-    info->n_edges = tp.n_edges;
-    info->n_faces = tp.n_faces;
-    int64_t nd = 0;
-    if (level == 1) {
-      for (uint8_t d : c->mesh.dir_h) nd += d ? 0 : 1;
-      nd *= c->mesh.dpn;
-    } else {
-      nd = tp.n_dofs;
-    }
-    info->n_dofs = nd;
-    info->n_coarse = tp.n_coarse;
-    for (const auto& sb : tp.subs) {
-      const double ni = sb.n_i, ng = sb.n_g, ndl = sb.n_d();
-      info->sum_ni += sb.n_i;
-      info->sum_ngamma += sb.n_g;
-      info->max_ni = std::max<int64_t>(info->max_ni, sb.n_i);
-      info->max_ngamma = std::max<int64_t>(info->max_ngamma, sb.n_g);
-      info->max_ndelta = std::max<int64_t>(info->max_ndelta, sb.n_d());
-      info->factor_flops += ni * ni * ni / 3.0 + ni * ni * ng + ni * ng * ng + ndl * ndl * ndl / 3.0;
-      info->schur_words += ng * ng;
-    }
+    const int64_t nd = level == 1 ? free_dofs(c->mesh.dir_h.data(), (int64_t)c->mesh.dir_h.size(), c->mesh.dpn)
+                                  : tp.n_dofs;
+    fill_sizes(tp, nd, info);
   });
+}
+
+int amb_plan_level1(const amb_mesh* mesh, const amb_partition* part, int32_t initial_constraints,
+                    amb_level_sizes* info, int32_t* sub_sizes) {
+  try {
+    AMB_CHECK(mesh && part && info, AMB_EINVAL, "NULL argument");
+    AMB_CHECK(mesh->nx >= 1 && mesh->ny >= 1 && mesh->nz >= 1, AMB_EINVAL, "invalid mesh size");
+    AMB_CHECK(mesh->dofs_per_node == 1 || mesh->dofs_per_node == 3, AMB_EINVAL, "dofs_per_node must be 1 or 3");
+    AMB_CHECK(initial_constraints == AMB_CORNERS || initial_constraints == AMB_CORNERS_EDGES, AMB_EINVAL,
+              "unknown initial constraints");
+    AMB_CHECK(mesh->dirichlet_node_mask && part->elem_to_sub, AMB_EINVAL, "NULL array");
+    AMB_CHECK(part->n_sub1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
+    validate_partition(mesh->nx, mesh->ny, mesh->nz, part->elem_to_sub, {}, {part->n_sub1});
+    std::vector<int32_t> elem_local;
+    const LevelTopo tp = build_level_one(mesh->nx, mesh->ny, mesh->nz, mesh->dofs_per_node,
+                                         mesh->dirichlet_node_mask, part->elem_to_sub, part->n_sub1,
+                                         initial_constraints, elem_local);
+    const int64_t nnodes = (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
+    fill_sizes(tp, free_dofs(mesh->dirichlet_node_mask, nnodes, mesh->dofs_per_node), info);
+    if (sub_sizes)
+      for (int s = 0; s < tp.n_subs; ++s) {
+        const SubTopo& sb = tp.subs[s];
+        sub_sizes[4 * s + 0] = sb.n_i;
+        sub_sizes[4 * s + 1] = sb.n_g;
+        sub_sizes[4 * s + 2] = sb.n_crn;
+        sub_sizes[4 * s + 3] = sb.n_c();
+      }
+    return AMB_OK;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (const std::exception&) {
+    return AMB_EINVAL;
+  }
 }
 
 int amb_export(const amb_ctx* cc, int32_t what, int32_t level, int32_t index, void* out, size_t* nbytes) {

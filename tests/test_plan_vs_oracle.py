@@ -1,0 +1,57 @@
+"""The library's host combinatorics (amb_plan_level1: Sec. 2 classification
+with the box-vertex corner rule, the initial constraints of Sec. 7.1)
+against the oracle's level, on the CPU: counts of substructures, faces,
+edges, corner nodes, free and coarse dofs, and per substructure n_I,
+n_Gamma, corner dofs and initial coarse dofs.  Irregular and ragged box
+partitions, substructures without interior dofs, scalar and elasticity
+problems, both initial constraint sets."""
+import numpy as np
+import pytest
+
+import amb_inputs as ai
+from oracle import levels as olv, pair as opr
+
+
+def _cases():
+    rng = np.random.default_rng(np.random.PCG64(7))
+    yield "toy221", ai.toy(3, 1, 1, split=(2, 2, 1))
+    yield "toy222_elast", ai.toy(2, 3, 2, split=(2, 2, 2))
+    yield "ragged", ai._make("ragged", 9, None, 1, np.ones(729), 2, 10.0,
+                             cuts1=[np.array([0, 2, 5, 9]), np.array([0, 4, 9]), np.array([0, 9])])
+    yield "thin", ai._make("thin", 6, None, 1, np.ones(216), 2, 10.0,
+                           cuts1=[np.array([0, 1, 4, 5, 6]), np.array([0, 3, 6]), np.array([0, 6])])
+    cuts = [ai.irregular_cuts(14, 4, 2, 5, rng) for _ in range(3)]
+    yield "irregular", ai._make("irr", 14, None, 1, np.ones(14 ** 3), 2, 10.0, cuts1=cuts)
+    cuts = [ai.irregular_cuts(10, 3, 2, 5, rng) for _ in range(3)]
+    yield "irregular_elast", ai._make("irr3", 10, None, 3, np.ones(1000), 2, 10.0, cuts1=cuts)
+
+
+@pytest.mark.parametrize("initial", ["ce", "c"])
+@pytest.mark.parametrize("name,prob", list(_cases()))
+def test_level_one_plan_matches_oracle(name, prob, initial):
+    from paper_1301_0191_gb300 import binding as B
+    info, subs = B.plan_level1(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
+                               prob.elem_to_sub, prob.n_subs(1),
+                               B.CORNERS_EDGES if initial == "ce" else B.CORNERS)
+    lev = olv.level_one(prob, initial=initial)
+    assert info.n_subs == lev.n_subs
+    assert info.n_dofs == lev.n
+    assert info.n_corner_nodes == int(lev.node_corner.sum())
+    assert info.n_edges == len(lev.edges)
+    assert info.n_pairs == len(opr.pairs_of(lev))
+    assert info.n_coarse == lev.n_coarse
+    for s, sb in enumerate(lev.subs):
+        n_crn = int(np.sum(lev.node_corner[lev.node_of_dof[sb.gdofs]]))
+        assert tuple(subs[s]) == (sb.n_i, sb.n_g, n_crn, sb.c.shape[0]), (name, s)
+    assert info.sum_ni == sum(sb.n_i for sb in lev.subs)
+    assert info.schur_words == float(sum(sb.n_g ** 2 for sb in lev.subs))
+
+
+def test_plan_rejects_a_non_box_partition():
+    from paper_1301_0191_gb300 import binding as B
+    prob = ai.toy(2, 1, 3, split=(2, 1, 1))
+    e2s = prob.elem_to_sub.copy()
+    e2s[0] = 1 - e2s[0]
+    with pytest.raises(B.AmbError) as ei:
+        B.plan_level1(prob.nx, prob.ny, prob.nz, 1, prob.dirichlet_node_mask, e2s, 2)
+    assert ei.value.status == B.EINVAL
