@@ -87,3 +87,33 @@ def test_lanczos_condition_estimate():
     f = fe.load_vector(prob)
     res = solver.pcg(h.ops[0], f, h.apply, rtol=1e-14, maxit=400)
     assert abs(res.cond - ev.max() / ev.min()) < 1e-3 * ev.max()
+
+
+def test_lower_tau_nests_constraints_and_lowers_lambda_max():
+    """Lowering tau adds rows per face (the selected eigenvectors of a higher
+    tau stay selected, so the constrained spaces are nested) and can only
+    lower the largest eigenvalue of M A, which is the maximum of the
+    averaging energy over the constrained space (Sec. 4); the smallest stays
+    >= 1.  Adaptivity on this 1e4-contrast problem lowers the PCG iteration
+    count against the initial constraints alone, and rows are capped per
+    face (the paper's saturation at the cap)."""
+    rng = np.random.default_rng(np.random.PCG64(81))
+    prob = ai.toy(4, 1, 81, split=(2, 2, 1), sigma=0.0)
+    prob.coeff = np.where(rng.random(prob.coeff.size) < 0.15, 1.0e4, 1.0)
+    f = fe.load_vector(prob)
+    lmax, rows, its = [], [], []
+    for tau in (1e30, 30.0, 6.0, 2.0):
+        h = solver.Hierarchy(prob, adaptive=True, tau=tau)
+        ev, _ = _dense_precond_spectrum(h)
+        assert ev.min() >= 1.0 - 1e-10
+        lmax.append(ev.max())
+        rows.append([int(k) for k in h.reports[0].n_selected])
+        its.append(solver.pcg(h.ops[0], f, h.apply, rtol=1e-8).its)
+    for a, b in zip(rows, rows[1:]):
+        assert all(x <= y for x, y in zip(a, b))
+    assert sum(rows[-1]) > sum(rows[0]) == 0
+    for a, b in zip(lmax, lmax[1:]):
+        assert b <= a * (1 + 1e-9)
+    assert lmax[-1] < lmax[0] and its[-1] < its[0]
+    hc = solver.Hierarchy(prob, adaptive=True, tau=1.01, max_per_face=2)
+    assert max(hc.reports[0].n_selected) == 2
