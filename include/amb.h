@@ -247,20 +247,23 @@ typedef struct {
 } amb_level_sizes;
 int amb_level_info(const amb_ctx* ctx, int32_t level, amb_level_sizes* info);
 
-/* Host-only plan of level 1, without a context and without any device work:
- * the classification of Sec. 2 (interface, faces, edges, box-vertex
- * corners) and the initial constraints of Sec. 7.1, for sizing a run
- * before amb_setup (device memory grows with sum n_I^2 and schur_words).
- * info receives what amb_level_info(ctx, 1, ...) reports for the same input
- * before adaptivity: n_coarse counts the initial coarse dofs only.
- * sub_sizes: NULL, or [host] 4 * n_sub1 int32 receiving per substructure
- * (n_I, n_Gamma, corner dofs, initial coarse dofs).  mesh, part: as for
- * amb_setup; only dofs_per_node, the sizes, the Dirichlet mask and
- * elem_to_sub are read (coefficients are not needed).  Errors: AMB_EINVAL
- * for NULL arguments, an unknown initial_constraints or a partition that
- * amb_setup would reject. */
-int amb_plan_level1(const amb_mesh* mesh, const amb_partition* part, int32_t initial_constraints,
-                    amb_level_sizes* info, int32_t* sub_sizes);
+/* Host-only plan of one level, without a context and without any device
+ * work: the classification of Sec. 2 (interface, faces, edges, box-vertex
+ * corners; on level i >= 2 the nodes are the coarse objects of level i-1,
+ * Sec. 3) and the initial constraints of Sec. 7.1, for sizing a run before
+ * amb_setup (device memory grows with sum n_I^2 and schur_words).
+ * Adaptive rows are not known before the eigenproblems, so the plan is that
+ * of the hierarchy with the initial constraints only: level 1 equals what
+ * amb_level_info(ctx, 1, ...) reports except that n_coarse counts the
+ * initial coarse dofs; levels >= 2 equal those of a set-up with adaptive = 0.
+ * level in [1, levels - 1].  sub_sizes: NULL, or [host] 4 * (substructures
+ * on that level) int32 receiving per substructure (n_I, n_Gamma, corner
+ * dofs, coarse dofs).  mesh, part: as for amb_setup; only dofs_per_node,
+ * the sizes, the Dirichlet mask and the partition are read.  Errors:
+ * AMB_EINVAL for NULL arguments, an unknown initial_constraints, a level out
+ * of range or a partition that amb_setup would reject. */
+int amb_plan(const amb_mesh* mesh, const amb_partition* part, int32_t levels, int32_t initial_constraints,
+             int32_t level, amb_level_sizes* info, int32_t* sub_sizes);
 
 /* Export internal results for verification.  Two-call size query as in
  * amb_eigen_report.  `what`:

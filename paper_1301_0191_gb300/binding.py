@@ -97,14 +97,14 @@ def lib():
         L.amb_schur_apply_noalloc.argtypes = [vp, i32, i32, vp, vp]
         L.amb_schur_apply_noalloc.restype = C.c_int
         L.amb_level_info.argtypes = [vp, i32, C.POINTER(LevelSizes)]
-        L.amb_plan_level1.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), i32, C.POINTER(LevelSizes), vp]
+        L.amb_plan.argtypes = [C.POINTER(Mesh), C.POINTER(Partition), i32, i32, i32, C.POINTER(LevelSizes), vp]
         L.amb_export.argtypes = [vp, i32, i32, i32, vp, sz]
         L.amb_stats.argtypes = [vp, C.POINTER(KernelStats)]
         L.amb_last_error.argtypes = [vp]
         L.amb_last_error.restype = C.c_char_p
         L.amb_destroy.argtypes = [vp]
         for f in ("amb_setup", "amb_solve", "amb_load_vector", "amb_eigen_report", "amb_grad", "amb_schur_apply",
-                  "amb_level_info", "amb_plan_level1", "amb_export", "amb_stats"):
+                  "amb_level_info", "amb_plan", "amb_export", "amb_stats"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -135,18 +135,24 @@ def default_options(**kw) -> Options:
     return o
 
 
-def plan_level1(nx, ny, nz, dofs_per_node, dirichlet_node_mask, elem_to_sub, n_sub1, initial=CORNERS_EDGES):
-    """Host-only level-1 plan (amb_plan_level1): the level's sizes and, per
-    substructure, (n_I, n_Gamma, corner dofs, initial coarse dofs).  No GPU."""
+def plan(nx, ny, nz, dofs_per_node, dirichlet_node_mask, elem_to_sub, n_sub1, levels=2, sub_to_parent=(),
+         n_sub=(), level=1, initial=CORNERS_EDGES):
+    """Host-only plan of one level with the initial constraints (amb_plan):
+    the level's sizes and, per substructure, (n_I, n_Gamma, corner dofs,
+    coarse dofs).  No GPU."""
     mask = np.ascontiguousarray(dirichlet_node_mask, dtype=np.uint8)
     e2s = np.ascontiguousarray(elem_to_sub, dtype=np.int32)
+    parents = [np.ascontiguousarray(p, dtype=np.int32) for p in sub_to_parent]
+    arr = (C.c_void_p * max(1, len(parents)))(*[_ptr(p) for p in parents])
+    ns = np.ascontiguousarray(list(n_sub) or [0], dtype=np.int32)
     mesh = Mesh(nx, ny, nz, 1.0 / nx, dofs_per_node, _ptr(mask))
-    part = Partition(_ptr(e2s), n_sub1, None, None)
+    part = Partition(_ptr(e2s), n_sub1, C.cast(arr, C.c_void_p) if parents else None, _ptr(ns) if parents else None)
+    n_level = ([n_sub1] + [int(v) for v in n_sub])[level - 1] if 1 <= level <= len(parents) + 1 else 1
     info = LevelSizes()
-    subs = np.zeros((n_sub1, 4), dtype=np.int32)
-    st = lib().amb_plan_level1(C.byref(mesh), C.byref(part), initial, C.byref(info), _ptr(subs))
+    subs = np.zeros((n_level, 4), dtype=np.int32)
+    st = lib().amb_plan(C.byref(mesh), C.byref(part), levels, initial, level, C.byref(info), _ptr(subs))
     if st != OK:
-        raise AmbError(st, "amb_plan_level1 rejected the input")
+        raise AmbError(st, "amb_plan rejected the input")
     return info, subs
 
 

@@ -418,23 +418,36 @@ int amb_level_info(const amb_ctx* cc, int32_t level, amb_level_sizes* info) {
   });
 }
 
-int amb_plan_level1(const amb_mesh* mesh, const amb_partition* part, int32_t initial_constraints,
-                    amb_level_sizes* info, int32_t* sub_sizes) {
+int amb_plan(const amb_mesh* mesh, const amb_partition* part, int32_t levels, int32_t initial_constraints,
+             int32_t level, amb_level_sizes* info, int32_t* sub_sizes) {
   try {
     AMB_CHECK(mesh && part && info, AMB_EINVAL, "NULL argument");
     AMB_CHECK(mesh->nx >= 1 && mesh->ny >= 1 && mesh->nz >= 1, AMB_EINVAL, "invalid mesh size");
     AMB_CHECK(mesh->dofs_per_node == 1 || mesh->dofs_per_node == 3, AMB_EINVAL, "dofs_per_node must be 1 or 3");
+    AMB_CHECK(levels >= 2 && levels <= AMB_MAX_LEVELS, AMB_EINVAL, "levels must be in [2, 8]");
+    AMB_CHECK(level >= 1 && level <= levels - 1, AMB_EINVAL, "level out of range");
     AMB_CHECK(initial_constraints == AMB_CORNERS || initial_constraints == AMB_CORNERS_EDGES, AMB_EINVAL,
               "unknown initial constraints");
     AMB_CHECK(mesh->dirichlet_node_mask && part->elem_to_sub, AMB_EINVAL, "NULL array");
     AMB_CHECK(part->n_sub1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
-    validate_partition(mesh->nx, mesh->ny, mesh->nz, part->elem_to_sub, {}, {part->n_sub1});
-    std::vector<int32_t> elem_local;
-    const LevelTopo tp = build_level_one(mesh->nx, mesh->ny, mesh->nz, mesh->dofs_per_node,
-                                         mesh->dirichlet_node_mask, part->elem_to_sub, part->n_sub1,
-                                         initial_constraints, elem_local);
+    std::vector<int> nsubs{part->n_sub1};
+    std::vector<std::vector<int32_t>> parents;
+    for (int i = 0; i < levels - 2; ++i) {
+      AMB_CHECK(part->sub_to_parent && part->n_sub && part->sub_to_parent[i], AMB_EINVAL,
+                "sub_to_parent required for levels > 2");
+      parents.emplace_back(part->sub_to_parent[i], part->sub_to_parent[i] + nsubs.back());
+      nsubs.push_back(part->n_sub[i]);
+    }
+    validate_partition(mesh->nx, mesh->ny, mesh->nz, part->elem_to_sub, parents, nsubs);
+    std::vector<int32_t> loc;
+    LevelTopo tp = build_level_one(mesh->nx, mesh->ny, mesh->nz, mesh->dofs_per_node, mesh->dirichlet_node_mask,
+                                   part->elem_to_sub, part->n_sub1, initial_constraints, loc);
+    for (int l = 2; l <= level; ++l) {
+      LevelTopo next = build_level_next(tp, parents[l - 2].data(), nsubs[l - 1], initial_constraints, loc);
+      tp = std::move(next);
+    }
     const int64_t nnodes = (int64_t)(mesh->nx + 1) * (mesh->ny + 1) * (mesh->nz + 1);
-    fill_sizes(tp, free_dofs(mesh->dirichlet_node_mask, nnodes, mesh->dofs_per_node), info);
+    fill_sizes(tp, level == 1 ? free_dofs(mesh->dirichlet_node_mask, nnodes, mesh->dofs_per_node) : tp.n_dofs, info);
     if (sub_sizes)
       for (int s = 0; s < tp.n_subs; ++s) {
         const SubTopo& sb = tp.subs[s];

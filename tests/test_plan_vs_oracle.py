@@ -1,15 +1,16 @@
-"""The library's host combinatorics (amb_plan_level1: Sec. 2 classification
-with the box-vertex corner rule, the initial constraints of Sec. 7.1)
-against the oracle's level, on the CPU: counts of substructures, faces,
-edges, corner nodes, free and coarse dofs, and per substructure n_I,
-n_Gamma, corner dofs and initial coarse dofs.  Irregular and ragged box
-partitions, substructures without interior dofs, scalar and elasticity
-problems, both initial constraint sets."""
+"""The library's host combinatorics (amb_plan: Sec. 2 classification with
+the box-vertex corner rule, the initial constraints of Sec. 7.1, the
+level-(i+1) nodes from the level-i coarse objects of Sec. 3) against the
+oracle's levels, on the CPU: counts of substructures, faces, edges, corner
+nodes, level and coarse dofs, and per substructure n_I, n_Gamma, corner
+dofs and coarse dofs.  Irregular and ragged box partitions, substructures
+without interior dofs, scalar and elasticity problems, both initial
+constraint sets, and levels 2 and 3 of non-adaptive hierarchies."""
 import numpy as np
 import pytest
 
 import amb_inputs as ai
-from oracle import levels as olv, pair as opr
+from oracle import levels as olv, pair as opr, solver
 
 
 def _cases():
@@ -30,10 +31,14 @@ def _cases():
 @pytest.mark.parametrize("name,prob", list(_cases()))
 def test_level_one_plan_matches_oracle(name, prob, initial):
     from paper_1301_0191_gb300 import binding as B
-    info, subs = B.plan_level1(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
-                               prob.elem_to_sub, prob.n_subs(1),
-                               B.CORNERS_EDGES if initial == "ce" else B.CORNERS)
+    info, subs = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
+                        prob.elem_to_sub, prob.n_subs(1),
+                        initial=B.CORNERS_EDGES if initial == "ce" else B.CORNERS)
     lev = olv.level_one(prob, initial=initial)
+    _compare(info, subs, lev, name)
+
+
+def _compare(info, subs, lev, name):
     assert info.n_subs == lev.n_subs
     assert info.n_dofs == lev.n
     assert info.n_corner_nodes == int(lev.node_corner.sum())
@@ -53,5 +58,33 @@ def test_plan_rejects_a_non_box_partition():
     e2s = prob.elem_to_sub.copy()
     e2s[0] = 1 - e2s[0]
     with pytest.raises(B.AmbError) as ei:
-        B.plan_level1(prob.nx, prob.ny, prob.nz, 1, prob.dirichlet_node_mask, e2s, 2)
+        B.plan(prob.nx, prob.ny, prob.nz, 1, prob.dirichlet_node_mask, e2s, 2)
     assert ei.value.status == B.EINVAL
+
+
+def _multilevel_cases():
+    g3 = [np.array([0, 2, 4]), np.array([0, 2]), np.array([0, 1])]
+    yield "scalar_4x2x1_to_2", ai.toy(3, 1, 41, split=(4, 2, 1), levels=3, groups=g3)
+    g = [np.array([0, 2, 4])] * 3
+    yield "elast_4x4x4_to_2x2x2", ai.toy(2, 3, 42, split=(4, 4, 4), levels=3, groups=g)
+    yield "scalar_4x4x4_to_2x2x2", ai.toy(2, 1, 43, split=(4, 4, 4), levels=3, groups=g)
+    rng = np.random.default_rng(np.random.PCG64(44))
+    cuts = [ai.irregular_cuts(16, 4, 3, 5, rng) for _ in range(3)]
+    yield "irregular_to_2x2x2", ai._make("irr", 16, None, 1, np.ones(16 ** 3), 3, 10.0, groups=g, cuts1=cuts)
+
+
+@pytest.mark.parametrize("name,prob", list(_multilevel_cases()))
+def test_level_two_plan_matches_oracle(name, prob):
+    """Level 2 of a non-adaptive three-level hierarchy: the nodes are the
+    level-1 corners and edges, only level-1 corners may become corners."""
+    from paper_1301_0191_gb300 import binding as B
+    h = solver.Hierarchy(prob, adaptive=False)
+    info, subs = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
+                        prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
+                        n_sub=[prob.n_subs(2)], level=2)
+    _compare(info, subs, h.levels[1], name)
+    # level 1 of the same hierarchy
+    info1, subs1 = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
+                          prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
+                          n_sub=[prob.n_subs(2)], level=1)
+    _compare(info1, subs1, h.levels[0], name)
