@@ -343,6 +343,62 @@ void number_coarse(LevelTopo& L) {
     for (int64_t c : a.rc) p.cmap_s.push_back(pc[c]);
     for (int64_t c : b.rc) p.cmap_t.push_back(pc[c]);
   }
+  check_topology(L);
+}
+
+void check_topology(const LevelTopo& L) {
+  auto need = [](bool ok, const char* what) {
+    if (!ok) throw Error(AMB_EINVAL, std::string("internal topology check failed: ") + what);
+  };
+  const int64_t ni = (int64_t)L.iface_dofs.size();
+  need((int)L.subs.size() == L.n_subs, "substructure count");
+  need((int64_t)L.own_off.size() == ni + 1 && L.own_off[0] == 0, "owner offsets");
+  need(L.own_sub.size() == (size_t)L.own_off.back() && L.own_pos.size() == L.own_sub.size(), "owner lists");
+  need(L.gidx.size() == L.subs.size(), "interface index lists");
+  for (int s = 0; s < L.n_subs; ++s) {
+    const SubTopo& sb = L.subs[s];
+    need(sb.n_i >= 0 && sb.n_crn >= 0 && sb.n_crn <= sb.n_g, "substructure sizes");
+    need(sb.dofs.size() == (size_t)(sb.n_i + sb.n_g), "substructure dof list");
+    for (int64_t d : sb.dofs) need(d >= 0 && d < L.n_dofs, "substructure dof out of range");
+    need(L.gidx[s].size() == (size_t)sb.n_g, "interface index list length");
+    for (int l = 0; l < sb.n_g; ++l) {
+      const int j = L.gidx[s][l];
+      need(j >= 0 && j < ni && L.iface_dofs[j] == sb.dofs[sb.n_i + l], "interface index");
+    }
+    need(sb.rc.size() == (size_t)sb.n_crn + sb.crows.size(), "coarse dof list");
+    for (int64_t c : sb.rc) need(c >= 0 && c < L.n_coarse, "coarse dof out of range");
+    for (const auto& row : sb.crows)
+      for (const auto& e : row) need(e.first >= 0 && e.first < sb.n_d(), "constraint position out of range");
+  }
+  for (int64_t j = 0; j < ni; ++j) {
+    need(L.iface_dofs[j] >= 0 && L.iface_dofs[j] < L.n_dofs, "interface dof out of range");
+    need(L.own_off[j + 1] > L.own_off[j], "interface dof without owner");
+    for (int q = L.own_off[j]; q < L.own_off[j + 1]; ++q) {
+      const int s = L.own_sub[q], l = L.own_pos[q];
+      need(s >= 0 && s < L.n_subs && l >= 0 && l < L.subs[s].n_g && L.gidx[s][l] == j, "interface owner");
+    }
+  }
+  for (const PairTopo& p : L.pairs) {
+    need(p.s >= 0 && p.s < L.n_subs && p.t >= 0 && p.t < L.n_subs && p.s != p.t, "pair substructures");
+    const SubTopo& a = L.subs[p.s];
+    const SubTopo& b = L.subs[p.t];
+    need(p.ps.size() == p.pt.size(), "pair shared lists");
+    const int nf = (int)p.ps.size();
+    for (int k = 0; k < nf; ++k) {
+      need(p.ps[k] >= 0 && p.ps[k] < a.n_g && p.pt[k] >= 0 && p.pt[k] < b.n_g, "pair shared position");
+      need(a.dofs[a.n_i + p.ps[k]] == b.dofs[b.n_i + p.pt[k]], "pair shared dof");
+    }
+    need(p.face.size() == p.face_dofs.size(), "pair face list");
+    for (int f : p.face) need(f >= 0 && f < nf, "pair face entry");
+    need(!p.goff.empty() && p.goff[0] == 0 && (size_t)p.goff.back() == p.gent.size() &&
+             p.gw.size() == p.gent.size(), "pair jump groups");
+    for (size_t g = 1; g < p.goff.size(); ++g) need(p.goff[g] >= p.goff[g - 1], "pair jump group offsets");
+    for (int e : p.gent) need(e >= 0 && e < nf, "pair jump entry");
+    need(p.cmap_s.size() == a.rc.size() && p.cmap_t.size() == b.rc.size(), "pair coarse maps");
+    for (int c : p.cmap_s) need(c >= 0 && c < p.n_cpair, "pair coarse index");
+    for (int c : p.cmap_t) need(c >= 0 && c < p.n_cpair, "pair coarse index");
+  }
+  for (int64_t d : L.corner_dofs) need(d >= 0 && d < L.n_dofs, "corner dof out of range");
 }
 
 void add_adaptive_rows(LevelTopo& L, int pi, const std::vector<std::vector<double>>& rows) {

@@ -97,8 +97,17 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
 LevelTopo build_level_next(const LevelTopo& prev, const int32_t* parent, int n_subs, int initial,
                            std::vector<int32_t>& elem_local);
 
-// Number coarse dofs, fill per-substructure rc/crows and the pair data.
+// Number coarse dofs, fill per-substructure rc/crows and the pair data, then
+// check_topology.
 void number_coarse(LevelTopo& L);
+
+// Every index map the device kernels gather or scatter through is in range
+// and consistent (interface numbering and owners, constraint positions, the
+// pairs' shared positions, jump groups and coarse maps); throws
+// Error(AMB_EINVAL, "internal topology check failed: ...") otherwise, so a
+// fault in the host combinatorics stops the set-up before any kernel reads
+// out of bounds.
+void check_topology(const LevelTopo& L);
 
 // Append adaptive rows (functionals on the face dofs of pair p).
 void add_adaptive_rows(LevelTopo& L, int p, const std::vector<std::vector<double>>& rows);
