@@ -83,3 +83,17 @@ def test_setup_rejects_invalid_partitions(case):
                   levels, m["tau"], parents, nsub)
     assert ei.value.status == B.EINVAL
     assert words in str(ei.value)
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/amb.h is a C header: it compiles as C99 with -pedantic."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "check.c"
+    src.write_text('#include "amb.h"\nint main(void) { return 0; }\n')
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
+                        "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
