@@ -97,3 +97,61 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only",
                         "-I", os.path.join(ROOT, "include"), str(src)], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <stdlib.h>
+#include "amb.h"
+
+/* 8 x 4 x 4 Poisson mesh, x = 0 clamped, 2 x 1 x 1 boxes: plan level 1 from C */
+int main(void) {
+  enum { NX = 8, NY = 4, NZ = 4 };
+  static uint8_t mask[(NX + 1) * (NY + 1) * (NZ + 1)];
+  static int32_t e2s[NX * NY * NZ];
+  for (int k = 0; k <= NZ; ++k)
+    for (int j = 0; j <= NY; ++j)
+      for (int i = 0; i <= NX; ++i) mask[i + (NX + 1) * (j + (NY + 1) * k)] = (uint8_t)(i == 0);
+  for (int k = 0; k < NZ; ++k)
+    for (int j = 0; j < NY; ++j)
+      for (int i = 0; i < NX; ++i) e2s[i + NX * (j + NY * k)] = i >= NX / 2;
+  amb_mesh mesh = {NX, NY, NZ, 1.0 / NX, 1, mask};
+  amb_partition part = {e2s, 2, NULL, NULL};
+  amb_options opt;
+  amb_default_options(&opt);
+  amb_level_sizes info;
+  int32_t sizes[8];
+  int st = amb_plan(&mesh, &part, 2, opt.initial_constraints, 1, &info, sizes);
+  printf("%d %d %d %lld %lld %d %d %d %d\n", st, info.n_subs, info.n_pairs, (long long)info.n_dofs,
+         (long long)info.n_coarse, sizes[0], sizes[1], sizes[4], sizes[5]);
+  return st;
+}
+"""
+
+
+def test_plan_from_a_c_program(tmp_path):
+    """The boundary used from plain C: a C99 program links libamb.so and plans
+    a two-substructure mesh (host only, no GPU)."""
+    import shutil
+    import subprocess
+    from paper_1301_0191_gb300 import build
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lib = build.build()
+    src = tmp_path / "plan.c"
+    src.write_text(C_PROGRAM)
+    exe = tmp_path / "plan"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src),
+                        "-L", os.path.dirname(lib), "-lamb", "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    st, nsub, npair, ndof, ncoarse, ni0, ng0, ni1, ng1 = (int(v) for v in out.stdout.split())
+    # 9 x 5 x 5 nodes, the x = 0 plane clamped; the interface is the x = 4 plane
+    # (25 nodes), whose box vertices are its 4 corners; no edges; every other
+    # free node is interior to one box
+    assert (st, nsub, npair, ndof) == (0, 2, 1, 8 * 25)
+    assert ncoarse == 4 and ng0 == ng1 == 25
+    assert ni0 == 3 * 25 and ni1 == 4 * 25
