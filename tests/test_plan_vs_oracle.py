@@ -88,3 +88,29 @@ def test_level_two_plan_matches_oracle(name, prob):
                           prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
                           n_sub=[prob.n_subs(2)], level=1)
     _compare(info1, subs1, h.levels[0], name)
+
+
+def test_plan_rejects_bad_levels():
+    from paper_1301_0191_gb300 import binding as B
+    prob = list(_multilevel_cases())[0][1]
+    args = (prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask, prob.elem_to_sub,
+            prob.n_subs(1))
+    for level in (0, 3):
+        with pytest.raises(B.AmbError) as ei:
+            B.plan(*args, levels=3, sub_to_parent=prob.sub_to_parent, n_sub=[prob.n_subs(2)], level=level)
+        assert ei.value.status == B.EINVAL
+    with pytest.raises(B.AmbError) as ei:                  # three levels need the parent map
+        B.plan(*args, levels=3, level=1)
+    assert ei.value.status == B.EINVAL
+
+
+@pytest.mark.parametrize("name,prob", list(_multilevel_cases())[:2])
+def test_level_two_plan_corners_only(name, prob):
+    """Level 2 with corners as the only initial constraints: its nodes are
+    the level-1 corners alone."""
+    from paper_1301_0191_gb300 import binding as B
+    h = solver.Hierarchy(prob, adaptive=False, initial="c")
+    info, subs = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
+                        prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
+                        n_sub=[prob.n_subs(2)], level=2, initial=B.CORNERS)
+    _compare(info, subs, h.levels[1], name)
