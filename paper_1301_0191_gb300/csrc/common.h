@@ -44,7 +44,7 @@ extern thread_local int64_t g_launches;
 
 // Device memory comes from the device's stream-ordered pool (cudaMallocAsync)
 // with no release threshold: buffers freed by one context are reused by the
-// next without returning to the driver, and a free does not synchronize the
+// next without returning to the CUDA driver, and a free does not synchronize the
 // device (cudaFree does).  Allocations and frees are ordered on the stream of
 // the context that the calling thread is serving (set at every ABI entry).
 inline cudaStream_t& alloc_stream() {
