@@ -114,3 +114,20 @@ def test_level_two_plan_corners_only(name, prob):
                         prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
                         n_sub=[prob.n_subs(2)], level=2, initial=B.CORNERS)
     _compare(info, subs, h.levels[1], name)
+
+
+def test_bench_workload_sizes():
+    """The 48^3 elasticity workload (4 x 4 x 4 boxes of 12^3 elements, the
+    x = 0 node plane clamped), by counting nodes: a box's nodes on outer,
+    unclamped faces are its own, so a box at the far corner has 12^3
+    interior nodes and a box with no free outer face 11^3.  The
+    factorization work equals the bench line's algorithmic flop count, which
+    came from the same sizes through amb_level_info on the GPU."""
+    from paper_1301_0191_gb300 import binding as B
+    p = ai.config(2)
+    info, subs = B.plan(p.nx, p.ny, p.nz, p.dofs_per_node, p.dirichlet_node_mask, p.elem_to_sub, p.n_subs(1))
+    assert (info.n_subs, info.n_pairs) == (64, 144)
+    assert info.n_dofs == 3 * 48 * 49 * 49                     # the x = 0 node plane is clamped
+    assert info.max_ni == 3 * 12 ** 3 and int(subs[:, 0].min()) == 3 * 11 ** 3
+    assert (info.max_ngamma, info.max_ndelta) == (2598, 2574)
+    assert info.factor_flops == 5776528886316.0
