@@ -112,3 +112,24 @@ def test_box_vertex_corners_ragged_and_level_two():
     # level 1 (cuts x 0,3,6,9,12; y 0,3,6; z 0,3): x = 3, 6, 9 give 3 x 3 x 2 = 18, x = 12 only y = 3 -> 20
     assert int(h.levels[0].node_corner.sum()) == 20
     assert int(h.levels[1].node_corner.sum()) == 4
+
+
+@pytest.mark.parametrize("dpn,split,initial", [(1, (2, 2, 1), "ce"), (3, (2, 2, 1), "ce"), (3, (2, 2, 2), "c")])
+def test_assumption_1_constrained_problems_are_definite(dpn, split, initial):
+    """Assumption 1: with the initial constraints every substructure's
+    energy is positive on the constrained space null(C), floating or not,
+    although S itself is singular for floating substructures (constants,
+    rigid modes).  Without constraints a floating substructure breaks it."""
+    import scipy.linalg as sla
+    prob = ai.toy(3, dpn, 17, split=split)
+    lev = lv.level_one(prob, initial)
+    lev.schur()
+    floating = 0
+    for sb in lev.subs:
+        z = sla.null_space(sb.c)
+        lam = np.linalg.eigvalsh(z.T @ sb.s @ z)
+        assert lam.min() > 1e-8 * lam.max()
+        lam_s = np.linalg.eigvalsh(sb.s)
+        if lam_s.min() < 1e-10 * lam_s.max():
+            floating += 1
+    assert floating > 0          # the case the assumption is about is present
