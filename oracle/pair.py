@@ -166,7 +166,10 @@ def rows_from_reduced(nmat, jumps, info):
 def face_rows(crows_f, info, lev):
     """Drop entries off the face-class dofs, orthonormalize (reduced QR).
 
-    Pinned by test_oracle_pair.py::test_corollary1_added_rows.
+    Pinned by test_oracle_face_rows.py (2x2x1 and 2x2x2 meshes, whose faces
+    border edges and corners): the support equals the face nodes' free dofs
+    found by brute force from the partition, the rows are orthonormal and
+    span the face-restricted c_l; and by test_oracle_pair.py::test_corollary1_added_rows.
     """
     f = info["f"]
     face_dofs = info["face_dofs"]
