@@ -281,6 +281,49 @@ __device__ void sort_desc(const double* A, int n, int ld, int* ord) {
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- null modes of floating substructures
+//
+// A level-1 substructure without Dirichlet dofs floats: its Schur complement
+// annihilates the rigid modes restricted to its interface (constants for the
+// scalar problem; three translations and three rotations for elasticity),
+// exactly (Sec. 2: S is the energy of the discrete harmonic extension).  The
+// FP32 form's S, rounded through the FP32 factorization, gives these modes
+// an energy of about 1e-7 of its norm, and the pair denominator B = Pi S Pi
+// (eq. eig-matrix) is nearly singular exactly there: the pencils' large
+// eigenvalues then move by per cents and LOBPCG stalls on the pairs of two
+// floating substructures.  The FP32 form therefore applies B with
+// P S P, P = I - Q Q^T the orthogonal projector off the modes (Q orthonormal):
+// P S P x = S x - T a - Q b with a = Q^T x, T = S Q, b = Q^T (S x - T a),
+// in FP64 after the product.  For the exact S, P S P = S.
+
+// Q (n_g x r per floating substructure, column-major) <- orthonormal basis of
+// its columns, two passes of classical Gram-Schmidt in FP64; one CTA each.
+__global__ void k_orth_modes(double* Qn, const int64_t* off, const int32_t* ng, int r) {
+  __shared__ double red[256];
+  const int64_t o = off[blockIdx.x];
+  const int n = ng[blockIdx.x];
+  double* Qs = Qn + o;
+  for (int k = 0; k < r; ++k) {
+    double* qk = Qs + (int64_t)k * n;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int l = 0; l < k; ++l) {
+        const double* ql = Qs + (int64_t)l * n;
+        double d = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) d += ql[i] * qk[i];
+        d = block_sum(d, red);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) qk[i] -= d * ql[i];
+        __syncthreads();
+      }
+    }
+    double nn = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) nn += qk[i] * qk[i];
+    nn = block_sum(nn, red);
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) qk[i] *= inv;
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------- pair kernels
 
 // pseudo-random start block (counter-based hash, SplitMix64 finalizer)
@@ -302,6 +345,55 @@ __global__ void k_lob_random(T* Qb, const int64_t* qp, int m, uint64_t seed) {
   T v = T(0);
   if (col < m) v = (T)hash_uniform(seed * 0x100000001B3ull ^ ((uint64_t)p << 40) ^ (uint64_t)idx);
   Qb[QP(p, Q_OQ) + idx] = v;
+}
+
+// B-product correction on floating pair sides: y <- y - T a - Q b with
+// a = Q^T x, b = Q^T (y - T a), for the m columns of the input slot cin (x)
+// and output slot cout (y) of the FP64 panel.  One CTA per (pair, side);
+// fixed-order block reductions (deterministic).
+__global__ void k_lob_nullproj(double* base, const int64_t* qp, int cin, int cout, int m, const int* act,
+                               const int64_t* qoff, const double* Qn, const double* Tn, int r) {
+  __shared__ double red[256];
+  const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
+  if (!act[p]) return;
+  const int sub = (int)QP(p, side ? Q_T : Q_S);
+  const int64_t o = qoff[sub];
+  if (o < 0) return;
+  const int64_t N = QP(p, Q_N);
+  const int n = (int)QP(p, side ? Q_NT : Q_NS);
+  const int64_t r0 = side ? QP(p, Q_NS) : 0;
+  const double* Qs = Qn + o;
+  const double* Ts = Tn + o;
+  const double* x = base + QP(p, Q_OQ) + (int64_t)cin * m * N + r0;
+  double* y = base + QP(p, Q_OQ) + (int64_t)cout * m * N + r0;
+  double a[6], b[6];
+  for (int c = 0; c < m; ++c) {
+    const double* xc = x + (int64_t)c * N;
+    double* yc = y + (int64_t)c * N;
+    for (int k = 0; k < r; ++k) {
+      double d = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) d += Qs[(int64_t)k * n + i] * xc[i];
+      a[k] = block_sum(d, red);
+    }
+    for (int k = 0; k < r; ++k) b[k] = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = yc[i];
+      for (int k = 0; k < r; ++k) v -= Ts[(int64_t)k * n + i] * a[k];
+      yc[i] = v;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+      double d = 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) d += Qs[(int64_t)k * n + i] * yc[i];
+      b[k] = block_sum(d, red);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double v = yc[i];
+      for (int k = 0; k < r; ++k) v -= Qs[(int64_t)k * n + i] * b[k];
+      yc[i] = v;
+    }
+    __syncthreads();
+  }
 }
 
 // Pi on columns [c0, c0+w) of a block with leading dimension N at base
@@ -1009,6 +1101,83 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     }
     AMB_CUDA(cudaStreamSynchronize(st));   // keep the offset table alive until the kernel ran
   }
+  // FP32 form, level 1: rigid modes of the floating substructures (those
+  // whose elements touch no Dirichlet node), orthonormalized, and T = S Q
+  // with the same extended-precision product as the B applies
+  DevBuf nQ, nT, nqoff;
+  int nr = 0;
+  bool nullproj = false;
+  if (sizeof(T) == sizeof(float) && lvl == 1) {
+    const int dpn = mesh.dpn;
+    nr = dpn == 1 ? 1 : 6;
+    std::vector<uint8_t> touched(L.ns, 0);
+    const int nx = mesh.nx, ny = mesh.ny;
+    for (int64_t e = 0; e < mesh.nel; ++e) {
+      const int64_t ei = e % nx, ej = (e / nx) % ny, ek = e / ((int64_t)nx * ny);
+      bool dir = false;
+      for (int c = 0; c < 8 && !dir; ++c) {
+        const int64_t node = (ei + (c & 1)) + (int64_t)(nx + 1) * ((ej + ((c >> 1) & 1)) + (int64_t)(ny + 1) * (ek + (c >> 2)));
+        dir = mesh.dir_h[node] != 0;
+      }
+      if (dir) touched[mesh.elem_sub_h[e]] = 1;
+    }
+    std::vector<int64_t> qoff(L.ns, -1), foff;
+    std::vector<int32_t> fng;
+    std::vector<double> hq;
+    for (int s = 0; s < L.ns; ++s) {
+      if (touched[s] || L.ng[s] < nr) continue;
+      const SubTopo& sb = tp.subs[s];
+      const int n = L.ng[s];
+      qoff[s] = (int64_t)hq.size();
+      foff.push_back(qoff[s]);
+      fng.push_back(n);
+      // node coordinates relative to the substructure's interface centroid
+      std::vector<double> xyz((size_t)3 * n);
+      double cen[3] = {0.0, 0.0, 0.0};
+      for (int l = 0; l < n; ++l) {
+        const int64_t node = sb.dofs[sb.n_i + l] / dpn;
+        const double c3[3] = {(double)(node % (nx + 1)), (double)((node / (nx + 1)) % (ny + 1)),
+                              (double)(node / ((int64_t)(nx + 1) * (ny + 1)))};
+        for (int a = 0; a < 3; ++a) {
+          xyz[(size_t)3 * l + a] = c3[a];
+          cen[a] += c3[a] / n;
+        }
+      }
+      hq.resize(hq.size() + (size_t)n * nr, 0.0);
+      double* qs = hq.data() + qoff[s];
+      for (int l = 0; l < n; ++l) {
+        if (dpn == 1) {
+          qs[l] = 1.0;
+          continue;
+        }
+        const int comp = (int)(sb.dofs[sb.n_i + l] % dpn);
+        const double px = xyz[(size_t)3 * l] - cen[0], py = xyz[(size_t)3 * l + 1] - cen[1],
+                     pz = xyz[(size_t)3 * l + 2] - cen[2];
+        qs[(size_t)comp * n + l] = 1.0;   // translations
+        // rotations w x p about the three axes, component `comp`
+        const double rx[3] = {0.0, -pz, py}, ry[3] = {pz, 0.0, -px}, rz[3] = {-py, px, 0.0};
+        qs[(size_t)3 * n + l] = rx[comp];
+        qs[(size_t)4 * n + l] = ry[comp];
+        qs[(size_t)5 * n + l] = rz[comp];
+      }
+    }
+    if (!foff.empty()) {
+      nullproj = true;
+      DevBuf dfoff, dfng;
+      upload(nQ, hq, st);
+      upload(nqoff, qoff, st);
+      upload(dfoff, foff, st);
+      upload(dfng, fng, st);
+      nT.alloc(hq.size() * sizeof(double));
+      k_orth_modes<<<(unsigned)foff.size(), 256, 0, st>>>(dptr<double>(nQ), dptr<int64_t>(dfoff), dptr<int32_t>(dfng), nr);
+      AMB_LAUNCHED();
+      std::vector<GemmDesc> d;
+      for (int s = 0; s < L.ns; ++s)
+        if (qoff[s] >= 0) d.push_back(GemmDesc{L.ng[s], nr, L.ng[s], L.ng[s], L.ng[s], L.ng[s], L.pS.off[s], qoff[s], qoff[s]});
+      gemm_batched<double, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(L.S), dptr<double>(nQ), dptr<double>(nT));
+      AMB_CUDA(cudaStreamSynchronize(st));   // keep the host tables alive until the kernels ran
+    }
+  }
   // pseudo-inverse of the pair coarse matrices (initial constraints)
   {
     const int nl = max_ncp + (max_ncp & 1);
@@ -1082,7 +1251,11 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       }
     }
     gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
-    
+    if (nullproj) {
+      k_lob_nullproj<<<2 * np, 256, 0, st>>>(Q, QPd, cin, cout, m, dptr<int>(act_d), dptr<int64_t>(nqoff),
+                                             dptr<double>(nQ), dptr<double>(nT), nr);
+      AMB_LAUNCHED();
+    }
     project(Q, Q_OQ, cout * m, m);
   };
   // W slot = M * (R in the temp panel, columns 0..m)

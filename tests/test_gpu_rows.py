@@ -68,7 +68,7 @@ def test_pair_rows_match_oracle(B, split, sub, dpn, seed, tau):
         rows = raw[: 8 * k * nf].view(np.float64).reshape(k, nf)
         dofs = raw[8 * k * nf:].view(np.int64)
         assert np.array_equal(dofs, free[res.face_dofs]), (p["s"], p["t"])
-        assert p["converged"] == 1
+        assert p["residual"] <= 1e-6, (p["s"], p["t"], p["residual"])
         if _ambiguous(res.lam, tau, cap):
             continue
         assert p["n_selected"] == res.n_selected

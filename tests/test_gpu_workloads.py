@@ -10,13 +10,18 @@ iterations within +-1 of the oracle.
 
 FP32 form (factorizations and preconditioner in FP32, trailing updates on the
 tensor cores in 3xTF32): the Schur complements carry FP32 rounding, which
-moves the pair eigenvalues that sit on near-null directions of S (the large
-ones) by up to a few per cent, and the iteration count of the 1e4-contrast
-workload grows by a few.  The bounds below are the measured behaviour with a
-margin: max eigenvalue deviation <= 5e-2 (measured 3.2e-2 and 3.6e-2), median
-<= 5e-3 (measured 1.8e-4 and 1.8e-3), selected rows per face identical
-within +-1, PCG iterations within +1 of the oracle (48^3: 38 vs 37; 16^3
-channels: 16 vs 15, the FP64 form's count).  The constraint space (G = C_D
+moves the pair eigenvalues that sit on near-null directions of S.  The
+rigid modes of floating substructures are projected out of the B products
+(exact for the FP64 S), which removes most of it: on the 48^3 elasticity
+workload the deviation is 1.3e-4 at most and 1.9e-6 in the median (3.2e-2 and
+1.8e-4 without the projection).  The 1e4-contrast channels have further
+near-null modes (the stiff channels inside floating substructures) that no
+projection removes: 3.0e-3 at most, 2.7e-4 in the median.  LOBPCG itself
+agrees with its own FP32 pencil to <= 1e-7 (test_gpu_fp32_form.py), so these
+are the FP32 pencil's errors.  Bounds (measured behaviour with a margin):
+48^3 max 5e-4, median 2e-5; 16^3 channels max 1e-2, median 2e-3; selected
+rows per face identical within +-1, PCG iterations within +1 of the oracle
+(48^3: 38 vs 37; 16^3 channels: 16 vs 15, the FP64 form's count).  The constraint space (G = C_D
 S_DD^-1 C_D^T, its inverse, the coarse basis) is FP64 in both forms; with it
 in FP32 the 1e4-contrast channels workload took 18 to 34 iterations depending
 on rounding order.
@@ -53,7 +58,7 @@ def _gold(i):
 
 @pytest.mark.parametrize("index,precision,rtol_max,rtol_med,it_slack",
                          [(1, "fp64", 1e-4, 1e-4, 1), (2, "fp64", 1e-4, 1e-4, 1),
-                          (1, "fp32", 5e-2, 5e-3, 1), (2, "fp32", 5e-2, 5e-3, 1)])
+                          (1, "fp32", 1e-2, 2e-3, 1), (2, "fp32", 5e-4, 2e-5, 1)])
 def test_workload_against_oracle(B, index, precision, rtol_max, rtol_med, it_slack):
     g = _gold(index)
     prob = ai.config(index)
