@@ -31,8 +31,8 @@ import amb_inputs as ai  # noqa: E402
 
 METRIC = "adaptive-BDDC setup+solve s to 1e-8 rel. residual; Schur-apply % of roofline"
 WORKLOAD = "elasticity48_4x4x4_lognormal"
-# DRAM bytes per 128 x 128 output tile of the tensor-core trailing update, from the ncu capture summarised in
-# profiles/k_tc_syrk_elasticity48_block2x2x2.md (one launch: 1,036,088,832 bytes over 7240 tiles; None when
+# DRAM bytes per 128 x 128 output tile of the tensor-core trailing update, from one ncu capture of that kernel
+# on the 2x2x2 corner block of the 48^3 workload (one launch: 1,036,088,832 bytes over 7240 tiles; None when
 # the kernel has changed since)
 TC_TRAFFIC_PER_TILE = 1036088832 / 7240
 TC_OUTER, TC_TILE = 256, 128
@@ -121,26 +121,40 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- oracle sample
-def oracle_sample(prob, reps=1):
-    """The CPU oracle on a bounded sample of the workload: set-up of the 2x2x1
-    block of substructures at the clamped face (24x24x12 elements, 4 of the 64
-    substructures, same coefficient field) and one Algorithm-1 application,
-    extrapolated to 64 substructures and the oracle's own iteration count on
-    the full workload (37, tests/golden)."""
+# PCG iterations of the oracle on the full workloads (tests/golden for 48^3; the 96^3 three-level workload is
+# too large for the whole oracle, so its estimate uses the library's FP64-form count, 30)
+ORACLE_ITS = {"c2": 37, "c3": 30}
+
+
+def oracle_sample(prob, its_full=37):
+    """The CPU oracle on a bounded sample of the workload, an ESTIMATE of the
+    whole oracle's time: set-up of the 2x2x1 block of level-1 substructures at
+    the clamped face (same substructure shapes and coefficient field) and one
+    Algorithm-1 application, scaled by (substructures / 4) and by the PCG
+    iteration count on the full workload."""
     from oracle import fe, solver
     sub = ai.sub_block(prob, (2, 2, 1))
-    its_full = 37   # the oracle's PCG iterations on the full workload (tests/golden)
     t0 = time.perf_counter()
     h = solver.Hierarchy(sub)
     t_setup = time.perf_counter() - t0
     f = fe.load_vector(sub)
     t1 = time.perf_counter()
     z = h.apply(f)
-    q = h.ops[0] @ z
+    _ = h.ops[0] @ z
     t_iter = time.perf_counter() - t1
-    scale = 64.0 / 4.0
+    scale = prob.n_subs(1) / 4.0
     est = scale * (t_setup + its_full * t_iter)
     return est, time.perf_counter() - t0, dict(t_setup=t_setup, t_iter=t_iter)
+
+
+def oracle_full_c1():
+    """The whole oracle (set-up of all 8 substructures, every pair eigenproblem, PCG to 1e-8) on the 16^3
+    channels workload, timed: a complete run, not an extrapolation."""
+    from oracle import solver
+    prob = ai.config(1)
+    t0 = time.perf_counter()
+    _, res, _ = solver.solve(prob)
+    return time.perf_counter() - t0, res.its
 
 
 def cpu_threads():
@@ -161,8 +175,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2block"],
-                    help="c2: the 48^3 workload; c2block: a corner block of its substructures (same shapes; "
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2block", "c3"],
+                    help="c2: the 48^3 elasticity workload; c3: the 96^3 Poisson workload on 512 irregular "
+                         "boxes, three levels; c2block: a corner block of the c2 substructures (same shapes; "
                          "2x1x1 holds ~0.5 GB on the device), for profiler captures")
     ap.add_argument("--block", default="2,1,1", help="substructures per axis of the c2block workload")
     ap.add_argument("--profile", action="store_true",
@@ -171,31 +186,34 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    prob = ai.config(2)
-    workload = WORKLOAD
+    prob = ai.config(3 if args.workload == "c3" else 2)
+    workload = prob.name
+    its_full = ORACLE_ITS["c3" if args.workload == "c3" else "c2"]
     if args.workload == "c2block":
         prob = ai.sub_block(prob, tuple(int(v) for v in args.block.split(",")))
         workload = prob.name
+    sample_desc = (f"ESTIMATE, not a complete run: oracle set-up of 4 of {prob.n_subs(1)} level-1 substructures "
+                   f"(2x2x1 block at the clamped face) + one Algorithm-1 application, scaled by "
+                   f"{prob.n_subs(1) / 4:g} and by {its_full} PCG iterations")
 
     if args.impl == "reference":
         if rank != 0:
             return
         for _ in range(args.warmup):
-            oracle_sample(prob)
+            oracle_sample(prob, its_full)
         vals, wall = [], 0.0
         for _ in range(args.steps):
-            est, w, _ = oracle_sample(prob)
+            est, w, _ = oracle_sample(prob, its_full)
             vals.append(est)
             wall += w
         v = statistics.mean(vals)
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * v, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "levels": 2, "tau": 10.0, "dofs": 345744},
+                "config": {"workload": workload, "levels": prob.levels, "tau": prob.tau},
+                "estimate": True,
                 "cpu_baseline": {"kind": "oracle", "value": v, "unit": "s", "cores": cpu_threads(),
-                                 "sample": "oracle set-up of 4 of 64 substructures (2x2x1 block at the clamped "
-                                           "face) + one Algorithm-1 application, scaled by 16 and by the "
-                                           "oracle's 37 iterations"},
+                                 "sample": sample_desc, "sample_wall_s_total": wall},
                 "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -296,18 +314,41 @@ def main():
                      if f_ms > 0 else None, "trtri_ms": fams["trtri"]["ms"],
                      "note": "factor family = Cholesky of A_II (whose trailing updates also form S) and of S_DD; "
                              "the explicit triangular inverses (trtri) are timed apart"}
-    # dominant factorization kernel: the tensor-core trailing update (FP32 form)
+    # the step's dominant kernel: the LOBPCG operator products (k_gemm_df, the A and B applies: FP32 S times
+    # the FP64 block with the sum carried in FP32 pairs on the SIMT units).  Algorithmic work: 2 n k w flops
+    # per product; algorithmic bytes: each substructure's S (B) and each pair side's S_ff (A) once per apply.
+    lop = fams["lobpcg_products"]
+    roofline = None
+    if lop["ms"] > 0:
+        ach = lop["flops"] / (lop["ms"] * 1e-3) / 1e12
+        gbs = lop["bytes"] / (lop["ms"] * 1e-3) / 1e9
+        roofline = {"kernel": "k_gemm_df: LOBPCG A and B products S X (factor-precision S, FP64 block, "
+                              "FP32-pair accumulation on the SIMT units)",
+                    "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                    "traffic": None,
+                    "traffic_note": "null: the ncu counters were taken before the last change of this kernel's "
+                                    "launch shapes",
+                    "algorithmic_GB/s": gbs, "hbm_frac_algorithmic": gbs / peaks["hbm_gbs"],
+                    "algorithmic_flops": lop["flops"], "algorithmic_bytes": lop["bytes"],
+                    "launches": lop["launches"], "ms": lop["ms"],
+                    "peak_source": "derived SIMT FP32 rate: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock "
+                                   f"{peaks.get('sm_max_mhz', 2070.0):g} MHz" if fp == "fp32" else
+                                   "nominal FP64 rate 1.25 TFLOP/s",
+                    "units": "flops = 2 per multiply-add of S X; each costs ~10 FP32 instructions in FP32 pairs, "
+                             "so frac <= ~0.2 at the issue limit"}
+    # the factorization's kernel: the tensor-core trailing update (FP32 form)
     tc = fams["tc_trailing"]
     if fp == "fp32" and tc["ms"] > 0:
         ach = tc["flops"] / (tc["ms"] * 1e-3) / 1e12
-        roofline = {"kernel": "k_tc_syrk (+ k_tc_split): Cholesky trailing update C -= P P^T, 3xTF32 on tcgen05",
+        roofline_factor = {"kernel": "k_tc_syrk (+ k_tc_split): Cholesky trailing update C -= P P^T, 3xTF32 on tcgen05",
                     "bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s", "frac": ach / tf32_peak,
                     "tensor_pipe_frac": 3.0 * ach / tf32_peak,
                     "traffic": TC_TRAFFIC_PER_TILE * tc_tiles(n_i, n_g, n_d) / (tc["launches"] // 2)
                     if TC_TRAFFIC_PER_TILE and tc["launches"] >= 2 else None,
                     "traffic_note": "k_tc_syrk DRAM bytes per launch (each update = one k_tc_split + one k_tc_syrk "
-                                    "launch): bytes per 128x128 tile from one ncu capture (48^3 corner block, 7240 "
-                                    "tiles) x this step's tiles / updates; the split pass is not included",
+                                    "launch): bytes per 128x128 tile from one ncu capture of one launch on the 2x2x2 "
+                                    "corner block (7240 tiles) x this step's tiles / updates; the split pass is not "
+                                    "included",
                     "algorithmic_bytes_per_tile": 2 * 4 * TC_TILE * TC_TILE,
                     "launches": tc["launches"], "ms": tc["ms"],
                     "peak_source": f"{src} bf16 dense burst x nominal TF32/BF16 ratio (of {src})",
@@ -315,7 +356,8 @@ def main():
                              "products of each"}
     else:
         achieved = fact_flops / (f_ms * 1e-3) / 1e12 if f_ms > 0 else None
-        roofline = {"kernel": "batched partial Cholesky (k_chol_diag + k_gemm panel/trailing, FP64)", "bound": "alu",
+        roofline_factor = {"kernel": "batched partial Cholesky (k_chol_diag + k_gemm panel/trailing, FP64)",
+                    "bound": "alu",
                     "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak if achieved else None, "traffic": None,
                     "peak_source": f"nominal {fp} rate"}
@@ -374,18 +416,35 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, wall, parts = oracle_sample(prob)
-        cpu = {"value": est, "unit": "s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": "oracle set-up of 4 of 64 substructures (2x2x1 block at the clamped face) + one "
-                         "Algorithm-1 application, scaled by 16 and by the oracle's 37 iterations",
-               "sample_wall_s": wall}
+        est, wall, parts = oracle_sample(prob, its_full)
+        cpu = {"value": est, "unit": "s", "cores": cpu_threads(), "kind": "oracle", "estimate": True,
+               "sample": sample_desc, "sample_wall_s": wall}
+        # one complete oracle run beside it (16^3 channels, two levels, adaptive), and the library on the same
+        # workload in both forms, set-up + solve, inputs on the host
+        t_or, its_or = oracle_full_c1()
+        p1 = ai.config(1)
+        gpu_s = {}
+        for name, pr1 in (("fp64", B.FP64), ("fp32", B.FP32)):
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                c1 = B.Context.from_problem(p1, precision=pr1, lobpcg_maxit=200, lobpcg_tol=1e-6)
+                f1 = c1.load_vector(p1.body)
+                _, i1 = c1.solve(f1)
+                c1.close()
+                torch.cuda.synchronize()
+                gpu_s[name] = {"s": time.perf_counter() - t0, "pcg_iterations": i1.iterations}
+        cpu["complete_run"] = {"workload": p1.name, "oracle_s": t_or, "oracle_pcg_iterations": its_or,
+                               "cores": cpu_threads(), "library_e2e": gpu_s,
+                               "note": "the whole oracle, set-up (all pair eigenproblems) + PCG to 1e-8, timed; "
+                                       "the library's times are the second of two runs, host inputs"}
     if rank == 0:
         last = infos[-1]
         line = {"metric": METRIC, "value": ms * 1e-3, "unit": "s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == B.FP32 else "f64",
                 "data": "synthetic",
-                "config": {"workload": workload, "levels": 2, "tau": 10.0, "dofs": int(li.n_dofs),
+                "config": {"workload": workload, "levels": prob.levels, "tau": prob.tau, "dofs": int(li.n_dofs),
                            "substructures": li.n_subs, "pairs": li.n_pairs, "l2": "working set >> L2 (no flush)",
                            "replicas": "one independent problem per GPU"},
                 "pcg_iterations": last.iterations, "rel_residual": last.rel_residual,
@@ -394,6 +453,7 @@ def main():
                 "phase_ms": st["phase_ms"],
                 "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
                 "gpu_launches": int(launches / args.steps), "clocks": clk, "roofline": roofline,
+                "roofline_factor": roofline_factor,
                 "schur_apply": schur, "factorization": factorization, "precond": precond,
                 "families": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in fams.items()},
                 "fp64_form": fp64_form, "cpu_baseline": cpu}

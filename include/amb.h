@@ -149,7 +149,10 @@ typedef struct {
 #define AMB_FAM_COARSE   6   /* coarse basis, coarse matrices and top factorization */
 #define AMB_FAM_TC       7   /* FP32 form: tensor-core trailing updates of the factorization
                                 (part of AMB_FAM_FACTOR; flops = rem (rem + 1) K per update) */
-#define AMB_FAM_N        8
+#define AMB_FAM_LOBOP    8   /* the LOBPCG operator products S X of the A and B applies (part of
+                                AMB_FAM_LOBPCG; flops = 2 n k w per product, bytes = the S blocks
+                                each apply reads once: sum n_G^2 (B) and sum n_f^2 (A) words) */
+#define AMB_FAM_N        9
 typedef struct {
   double ms[AMB_FAM_N];         /* summed event time */
   int64_t launches[AMB_FAM_N];  /* kernel launches counted in the family */
@@ -230,7 +233,15 @@ int amb_schur_apply(amb_ctx* ctx, int32_t level, int32_t width, const void* x, v
  * allocating call.  Limits: at most 1024 substructures on the level, else
  * AMB_EINVAL with a message.  The context's device must be current.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and caches it for the process; a device reset
+ * invalidates it, so do not call this after resetting the device.  The call
+ * copies its descriptors from host memory and waits for the context stream,
+ * so it must not be made while that stream (or, in global capture mode, any
+ * stream) is being captured: it returns AMB_EINVAL when the context stream
+ * is capturing.  The descriptors are built in per-thread host buffers (no
+ * large stack frame).  Unlike amb_schur_apply, this variant always runs the
+ * SIMT products: at FP32 widths >= 64 it does not use the tensor cores, so
+ * its results differ from amb_schur_apply's there by FP32 rounding.
  * All calls share the array and it keeps the last call's descriptors:
  * calls whose GPU work overlaps (other streams, other host threads) race on
  * it, so serialise them.  Returns after the context stream has finished. */

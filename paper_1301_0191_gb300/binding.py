@@ -18,9 +18,9 @@ OK, EINVAL, ENOMEM, ENOTSPD, EASSUMPTION, ENOCONV, ETIMEOUT, ECUDA = range(8)
 FP64, FP32 = 0, 1
 CORNERS, CORNERS_EDGES = 1, 2
 QOI_COMPLIANCE, QOI_GENERAL = 0, 1
-MAX_EIG, MAX_LEVELS, FAM_N = 16, 8, 8
+MAX_EIG, MAX_LEVELS, FAM_N = 16, 8, 9
 X_SUB_DOFS, X_SUB_SIZES, X_SCHUR, X_COARSE_EL, X_CONSTR, X_CORNERS, X_PAIR_ROWS = range(1, 8)
-FAMILIES = ("factor", "trtri", "schur", "lobpcg", "precond", "operator", "coarse", "tc_trailing")
+FAMILIES = ("factor", "trtri", "schur", "lobpcg", "precond", "operator", "coarse", "tc_trailing", "lobpcg_products")
 
 
 class Mesh(C.Structure):

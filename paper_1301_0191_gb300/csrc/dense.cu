@@ -315,7 +315,12 @@ template <typename T> struct GemmTile;
 template <> struct GemmTile<double> { static constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4; };
 template <> struct GemmTile<float> { static constexpr int BM = 128, BN = 128, BK = 16, TM = 8, TN = 8; };
 
-// Tile shapes: a wide one, and a skinny one for products whose right-hand
+// Tile shapes: a thin one (8 columns) for the soft-locked LOBPCG blocks, whose
+// active width is mostly the used columns plus a few guards;
+template <typename T> struct GemmThin;
+template <> struct GemmThin<double> { static constexpr int BM = 64, BN = 8, BK = 16, TM = 4, TN = 2; };
+template <> struct GemmThin<float> { static constexpr int BM = 128, BN = 8, BK = 16, TM = 8, TN = 2; };
+// a wide one, and a skinny one for products whose right-hand
 // block has at most 16 columns (the LOBPCG blocks and the Neumann solves of
 // the pair preconditioner), which would otherwise waste most of a wide tile.
 template <typename T> struct GemmSkinny;
@@ -385,7 +390,7 @@ static void gemm_run(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc
 // graph, take the static rule (narrowest tile that covers the columns).
 namespace {
 
-enum TileChoice { TILE_SKINNY = 0, TILE_MEDIUM = 1, TILE_HALF = 2, TILE_WIDE = 3 };
+enum TileChoice { TILE_THIN = 0, TILE_SKINNY = 1, TILE_MEDIUM = 2, TILE_HALF = 3, TILE_WIDE = 4 };
 
 struct TuneKey {
   int type, flags, ndesc, mmax, nmax, kmax;
@@ -413,6 +418,7 @@ template <typename T, typename TA>
 void run_choice(int c, cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& d, int flags, T alpha, T beta,
                 const TA* A, const T* B, T* C) {
   switch (c) {
+    case TILE_THIN: gemm_run<T, TA, GemmThin<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
     case TILE_SKINNY: gemm_run<T, TA, GemmSkinny<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
     case TILE_MEDIUM: gemm_run<T, TA, GemmMedium<T>>(st, ring, d, flags, alpha, beta, A, B, C); break;
     case TILE_HALF:
@@ -452,7 +458,8 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   const bool narrow_ok = !(flags & G_OUT_LOWER);
   // static rule
   int choice = TILE_WIDE;
-  if (narrow_ok && nmax <= 16) choice = TILE_SKINNY;
+  if (narrow_ok && nmax <= 8) choice = TILE_THIN;
+  else if (narrow_ok && nmax <= 16) choice = TILE_SKINNY;
   else if (narrow_ok && nmax <= 32) choice = TILE_MEDIUM;
   else if (std::is_same<T, float>::value && narrow_ok && nmax <= 64) choice = TILE_HALF;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -479,7 +486,7 @@ void gemm_batched(cudaStream_t st, DescRing& ring, const std::vector<GemmDesc>& 
   // candidates: every shape from the narrowest that covers the columns up
   // to the widest (a narrower tile than the columns runs more column tiles)
   std::vector<int> cand;
-  for (int c = TILE_SKINNY; c <= TILE_WIDE; ++c) {
+  for (int c = TILE_THIN; c <= TILE_WIDE; ++c) {
     if (c == TILE_HALF && !std::is_same<T, float>::value) continue;
     cand.push_back(c);
   }

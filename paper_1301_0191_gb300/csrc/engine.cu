@@ -705,10 +705,16 @@ void Engine<T>::schur_apply_staged(int level, int width, const void* x, void* y,
   const LevelData<T>& L = *lv[level - 1];
   AMB_CHECK(L.ns <= kStagedMaxDesc, AMB_EINVAL,
             "more than " + std::to_string(kStagedMaxDesc) + " substructures on the level");
-  // descriptors are built on the host stack: no heap or device allocation
-  GemmDesc gd[kStagedMaxDesc];
-  GemvDesc vd[kStagedMaxDesc];
-  int prefix[kStagedMaxDesc + 1];
+  // descriptors are built in per-thread host buffers of static storage
+  // (allocated on a thread's first call, never on the device); they are
+  // large (about 90 KB together), so they stay off the stack, whose size a
+  // caller's thread may limit
+  static thread_local std::vector<GemmDesc> gd_buf(kStagedMaxDesc);
+  static thread_local std::vector<GemvDesc> vd_buf(kStagedMaxDesc);
+  static thread_local std::vector<int> pre_buf(kStagedMaxDesc + 1);
+  GemmDesc* gd = gd_buf.data();
+  GemvDesc* vd = vd_buf.data();
+  int* prefix = pre_buf.data();
   int nd = 0, total = 0;
   int64_t off = 0;
   for (int s = 0; s < L.ns; ++s) {

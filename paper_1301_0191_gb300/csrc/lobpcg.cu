@@ -348,12 +348,13 @@ __global__ void k_lob_random(T* Qb, const int64_t* qp, int m, uint64_t seed) {
 }
 
 // B-product correction on floating pair sides: y <- y - T a - Q b with
-// a = Q^T x, b = Q^T (y - T a), for the m columns of the input slot cin (x)
-// and output slot cout (y) of the FP64 panel.  One CTA per (pair, side);
-// fixed-order block reductions (deterministic).
+// a = Q^T x, b = Q^T (y - T a), for the columns of the input slot cin (x)
+// and output slot cout (y) of the FP64 panel.  One CTA per (pair, side), one
+// warp per column (fixed-order lane sums and shuffles: deterministic, no
+// block barriers).  ncol: per pair, the number of leading columns that can
+// be nonzero (nullptr: all m).
 __global__ void k_lob_nullproj(double* base, const int64_t* qp, int cin, int cout, int m, const int* act,
-                               const int64_t* qoff, const double* Qn, const double* Tn, int r) {
-  __shared__ double red[256];
+                               const int64_t* qoff, const double* Qn, const double* Tn, int r, const int* ncol) {
   const int p = blockIdx.x >> 1, side = blockIdx.x & 1;
   if (!act[p]) return;
   const int sub = (int)QP(p, side ? Q_T : Q_S);
@@ -366,33 +367,41 @@ __global__ void k_lob_nullproj(double* base, const int64_t* qp, int cin, int cou
   const double* Ts = Tn + o;
   const double* x = base + QP(p, Q_OQ) + (int64_t)cin * m * N + r0;
   double* y = base + QP(p, Q_OQ) + (int64_t)cout * m * N + r0;
-  double a[6], b[6];
-  for (int c = 0; c < m; ++c) {
+  const int nc = ncol ? min(ncol[p], m) : m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nwarp) {
     const double* xc = x + (int64_t)c * N;
     double* yc = y + (int64_t)c * N;
-    for (int k = 0; k < r; ++k) {
-      double d = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) d += Qs[(int64_t)k * n + i] * xc[i];
-      a[k] = block_sum(d, red);
+    double a[6] = {0, 0, 0, 0, 0, 0}, b[6] = {0, 0, 0, 0, 0, 0};
+    for (int i = lane; i < n; i += 32) {
+      const double xv = xc[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) a[k] = fma(Qs[(int64_t)k * n + i], xv, a[k]);
     }
-    for (int k = 0; k < r; ++k) b[k] = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      for (int off = 16; off > 0; off >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+    for (int i = lane; i < n; i += 32) {
       double v = yc[i];
-      for (int k = 0; k < r; ++k) v -= Ts[(int64_t)k * n + i] * a[k];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) v = fma(-Ts[(int64_t)k * n + i], a[k], v);
+      yc[i] = v;
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) b[k] = fma(Qs[(int64_t)k * n + i], v, b[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      for (int off = 16; off > 0; off >>= 1) b[k] += __shfl_xor_sync(0xffffffffu, b[k], off);
+    for (int i = lane; i < n; i += 32) {
+      double v = yc[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) v = fma(-Qs[(int64_t)k * n + i], b[k], v);
       yc[i] = v;
     }
-    __syncthreads();
-    for (int k = 0; k < r; ++k) {
-      double d = 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) d += Qs[(int64_t)k * n + i] * yc[i];
-      b[k] = block_sum(d, red);
-    }
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      double v = yc[i];
-      for (int k = 0; k < r; ++k) v -= Qs[(int64_t)k * n + i] * b[k];
-      yc[i] = v;
-    }
-    __syncthreads();
   }
 }
 
@@ -626,10 +635,13 @@ __device__ __forceinline__ void df_mac(float& h, float& l, float2 x, float2 y) {
 }
 
 template <typename T>
-__global__ void k_lob_gram_part(double* part, const T* Qb, const int64_t* qp, int m, int w, const int* act,
-                                int nchunk) {
+__global__ void k_lob_gram_part(double* part, const T* Qb, const int64_t* qp, int m, int wfull, const int* act,
+                                int nchunk, const int* nwa) {
   const int p = blockIdx.x, kind = blockIdx.y, ch = blockIdx.z;
-  double* out = part + (((int64_t)p * 2 + kind) * nchunk + ch) * (int64_t)w * w;
+  double* out = part + (((int64_t)p * 2 + kind) * nchunk + ch) * (int64_t)wfull * wfull;
+  // compact active columns (soft locking): X, then the first nw of W and of P
+  const int nwp = wfull > m ? min(nwa[p], m) : 0;
+  const int w = m + nwp * (wfull / m - 1);
   const int nb = (w + 1) / 2, nblk = nb * (nb + 1) / 2;
   const int64_t N = QP(p, Q_N);
   const int64_t rb = (int64_t)ch * kGramRows, re = min(N, rb + kGramRows);
@@ -655,8 +667,9 @@ __global__ void k_lob_gram_part(double* part, const T* Qb, const int64_t* qp, in
     for (int idx = threadIdx.x; idx < 32 * wp; idx += blockDim.x) {
       const int r = idx % 32, c = idx / 32;
       const bool in = r < rn && c < w;
-      const double u = in ? (double)U[r0 + r + (int64_t)c * N] : 0.0;
-      const double v = in ? (double)Vb[r0 + r + (int64_t)c * N] : 0.0;
+      const int cc = c < m + nwp ? c : 2 * m + (c - m - nwp);
+      const double u = in ? (double)U[r0 + r + (int64_t)cc * N] : 0.0;
+      const double v = in ? (double)Vb[r0 + r + (int64_t)cc * N] : 0.0;
       const float uh = (float)u, vh = (float)v;
       us[r][c] = make_float2(uh, (float)(u - (double)uh));
       vs[r][c] = make_float2(vh, (float)(v - (double)vh));
@@ -684,18 +697,20 @@ __global__ void k_lob_gram_part(double* part, const T* Qb, const int64_t* qp, in
   }
 }
 
-__global__ void k_lob_gram_sum(double* G, const double* part, const int64_t* qp, int m, int w, const int* act,
-                               int nchunk) {
+__global__ void k_lob_gram_sum(double* G, const double* part, const int64_t* qp, int m, int wfull, const int* act,
+                               int nchunk, const int* nwa) {
   const int p = blockIdx.x, kind = blockIdx.y;
   if (!act[p]) return;
   const int m3 = 3 * m;
-  const double* in = part + ((int64_t)p * 2 + kind) * nchunk * (int64_t)w * w;
+  const int nwp = wfull > m ? min(nwa[p], m) : 0;
+  const int w = m + nwp * (wfull / m - 1);
+  const double* in = part + ((int64_t)p * 2 + kind) * nchunk * (int64_t)wfull * wfull;
   double* g = G + QP(p, Q_OGR) + (int64_t)kind * m3 * m3;
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     const int a = idx % w, b = idx / w;
     if (a > b) continue;
     double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += in[(int64_t)c * w * w + idx];
+    for (int c = 0; c < nchunk; ++c) s += in[(int64_t)c * wfull * wfull + idx];
     g[a + b * m3] = s;
     g[b + a * m3] = s;
   }
@@ -705,11 +720,18 @@ __global__ void k_lob_gram_sum(double* G, const double* part, const int64_t* qp,
 // reduced standard eigenproblem; coefficients Cc = [Cx | Cp] (3m x 2m, T)
 // and the m largest Ritz values.  Frozen pairs keep X (Cx = I, Cp = 0).
 template <typename T>
-__global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int w,
-                         double drop) {
+__global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int wfull,
+                         double drop, const int* nwa) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
   const int m3 = 3 * m;
+  // active basis columns: X (m), then the first nw columns of W and of P
+  // (soft locking: the other columns of W and P are zero or unused)
+  const int nwp = wfull > m ? min(nwa[p], m) : 0;
+  const int w = m + nwp * (wfull / m - 1);
+  __shared__ int cmap[3 * AMB_MAX_EIG];
+  for (int i = threadIdx.x; i < w; i += blockDim.x)
+    cmap[i] = i < m ? i : (i < m + nwp ? i : 2 * m + (i - m - nwp));
   const int ld = w + (w & 1);   // padded for the Jacobi rounds
   double* GA = sh;
   double* GB = GA + ld * ld;
@@ -731,6 +753,8 @@ __global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, c
   }
   const double* ga = G + QP(p, Q_OGR);
   const double* gb = ga + m3 * m3;
+  __syncthreads();
+  // the Gram matrices are stored in the compact column order
   for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
     int r = idx % w, c = idx / w;
     GA[r + c * ld] = 0.5 * (ga[r + c * m3] + ga[c + r * m3]);
@@ -796,17 +820,21 @@ __global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, c
   jacobi_eig(Mr, GB, r, ld, red, cs_, sn_, P_, Q_, GA, V);   // eigenvectors into GB (r x r, ld); GA, V: scratch
   sort_desc(Mr, r, ld, ord2);
   const int mm = min(m, r);
-  // Cx(:, k) = D Tm y_k ; Cp = Cx with the X rows zeroed
-  for (int idx = threadIdx.x; idx < m3 * m; idx += blockDim.x) {
-    int i = idx % m3, k = idx / m3;
+  // Cx(:, k) = D Tm y_k ; Cp = Cx with the X rows zeroed; rows of the
+  // inactive columns are zero
+  for (int idx = threadIdx.x; idx < m3 * 2 * m; idx += blockDim.x) C[idx] = T(0);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < w * m; idx += blockDim.x) {
+    int i = idx % w, k = idx / w;
     double s = 0.0;
-    if (i < w && k < mm) {
+    if (k < mm) {
       int c = ord2[k];
       for (int j = 0; j < r; ++j) s += Yr[i + j * ld] * GB[j + c * ld];
       s *= dsc[i];
     }
-    C[i + (int64_t)k * m3] = (T)s;
-    C[i + (int64_t)(m + k) * m3] = (i < m) ? T(0) : (T)s;
+    const int ri = cmap[i];
+    C[ri + (int64_t)k * m3] = (T)s;
+    C[ri + (int64_t)(m + k) * m3] = (ri < m) ? T(0) : (T)s;
   }
   if (threadIdx.x < m) {
     int k = threadIdx.x;
@@ -917,14 +945,16 @@ __global__ void k_lob_rows(double* rows, int* kept, const T* Qb, const int64_t* 
   }
 }
 
+// R (W slot) -> temp panel columns 0..m; columns >= nw[p] (soft-locked: no
+// new search direction) are zero, so that M R, A W and B W vanish there
 template <typename T>
-__global__ void k_lob_copy_w(T* Tp, const T* Qb, const int64_t* qp, int m, const int* act) {
+__global__ void k_lob_copy_w(T* Tp, const T* Qb, const int64_t* qp, int m, const int* act, const int* nw) {
   const int p = blockIdx.y;
   if (!act[p]) return;
   const int64_t N = QP(p, Q_N);
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= N * m) return;
-  Tp[QP(p, Q_OT) + idx] = Qb[QP(p, Q_OQ) + (int64_t)m * N + idx];
+  Tp[QP(p, Q_OT) + idx] = (idx / N < nw[p]) ? Qb[QP(p, Q_OQ) + (int64_t)m * N + idx] : T(0);
 }
 
 inline unsigned nblk(int64_t n) { return (unsigned)((n + 255) / 256); }
@@ -1078,6 +1108,20 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   rn.alloc((size_t)np * m * sizeof(double));
   bn.alloc((size_t)np * m * sizeof(double));
   act_d.alloc(np * sizeof(int));
+  // soft locking (FP32 form): per pair, the number of leading columns that
+  // get a new search direction (W) and keep a previous one (P) in the
+  // Rayleigh-Ritz basis: the used columns (the selected ones and the
+  // indicator) and kGuard more, which keep the last used column converging
+  // at the rate of a wider block; the other columns of X stay in the basis
+  // without them.  The FP64 form keeps the full block: the pairs of stiff
+  // slabs crossing a face (lambda_1 ~ 1e5 tau, whose eigenvector has a
+  // B-energy near 1e-13 of the operator's scale) converge there only with
+  // every column's search direction, and which rounding path reaches them is
+  // fragile.
+  const int kGuard = sizeof(T) == sizeof(float) ? 4 : m;
+  DevBuf nw_d;
+  nw_d.alloc(np * sizeof(int));
+  std::vector<int> nwh(np, m);
   rows.alloc(std::max<int64_t>(oR, 1) * sizeof(double));
   kept.alloc(np * sizeof(int));
   nsel_d.alloc(np * sizeof(int));
@@ -1214,7 +1258,10 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     AMB_LAUNCHED();
   };
   // out slot = A * (in slot); in and out are column blocks of the panel
+  // for the W slot (cin == 1) only the first nwh[p] columns are nonzero:
+  // the products run on those, and the outputs start from zero
   auto applyA = [&](int cin, int cout) {
+    if (cin == 1) AMB_CUDA(cudaMemsetAsync(Jb.p, 0, oJ * sizeof(V), st));
     k_lob_jump<V, V><<<dim3(nblk(maxnf * m), np), 256, 0, st>>>(dptr<V>(Jb), Q, QPd, Q_OQ, cin * m, m,
                                                                 dptr<int32_t>(dps), dptr<int32_t>(dpt),
                                                                 dptr<double>(dws), dptr<double>(dwt));
@@ -1224,12 +1271,20 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
       if (!active[p]) continue;
       const int nf = (int)q[Q_NF];
+      const int wcol = cin == 1 ? nwh[p] : m;
       for (int side = 0; side < 2; ++side)
-        d.push_back(GemmDesc{nf, m, nf, std::max(nf, 1), std::max(nf, 1), std::max(nf, 1),
+        d.push_back(GemmDesc{nf, wcol, nf, std::max(nf, 1), std::max(nf, 1), std::max(nf, 1),
                              q[Q_OF] + side * (int64_t)nf * nf, q[Q_OJ] + side * (int64_t)nf * m,
                              q[Q_OJ] + (2 + side) * (int64_t)nf * m});
     }
-    gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(Sff), dptr<V>(Jb), dptr<V>(Jb));
+    {
+      FamTimer fo(st, &tm, AMB_FAM_LOBOP, timing());
+      gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(Sff), dptr<V>(Jb), dptr<V>(Jb));
+      for (const GemmDesc& g : d) {
+        tm.fam_flops[AMB_FAM_LOBOP] += 2.0 * g.m * g.k * g.n;
+        tm.fam_bytes[AMB_FAM_LOBOP] += (double)sizeof(T) * g.m * g.k;
+      }
+    }
     k_lob_iet<V, V><<<dim3(np, m), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, dptr<V>(Jb), m, dptr<int32_t>(dps),
                                                 dptr<int32_t>(dpt), dptr<double>(dws), dptr<double>(dwt));
     AMB_LAUNCHED();
@@ -1237,6 +1292,10 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   };
   auto applyB = [&](int cin, int cout) {
     // FP32 operator entries, FP64 block vectors and accumulation
+    if (cin == 1) {
+      k_lob_zero<V><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(Q, QPd, Q_OQ, cout * m, m);
+      AMB_LAUNCHED();
+    }
     std::vector<GemmDesc> d;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
@@ -1246,14 +1305,33 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
         const int sub = (int)(side ? q[Q_T] : q[Q_S]);
         const int ng = L.ng[sub];
         const int64_t r0 = side ? q[Q_NS] : 0;
-        d.push_back(GemmDesc{ng, m, ng, std::max(ng, 1), (int)N, (int)N, L.pS.off[sub], q[Q_OQ] + cin * m * N + r0,
-                             q[Q_OQ] + cout * m * N + r0});
+        d.push_back(GemmDesc{ng, cin == 1 ? nwh[p] : m, ng, std::max(ng, 1), (int)N, (int)N, L.pS.off[sub],
+                             q[Q_OQ] + cin * m * N + r0, q[Q_OQ] + cout * m * N + r0});
       }
     }
-    gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+    {
+      FamTimer fo(st, &tm, AMB_FAM_LOBOP, timing());
+      gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+      std::vector<char> seen(L.ns, 0);
+      for (size_t i = 0; i < d.size(); ++i) {
+        const GemmDesc& g = d[i];
+        tm.fam_flops[AMB_FAM_LOBOP] += 2.0 * g.m * g.k * g.n;
+      }
+      // algorithmic bytes: every substructure's S once per apply
+      for (int p = 0; p < np; ++p) {
+        if (!active[p]) continue;
+        for (int side = 0; side < 2; ++side) {
+          const int sub = (int)qp[(size_t)p * Q_NPAIRF + (side ? Q_T : Q_S)];
+          if (seen[sub]) continue;
+          seen[sub] = 1;
+          tm.fam_bytes[AMB_FAM_LOBOP] += (double)sizeof(T) * L.ng[sub] * L.ng[sub];
+        }
+      }
+    }
     if (nullproj) {
       k_lob_nullproj<<<2 * np, 256, 0, st>>>(Q, QPd, cin, cout, m, dptr<int>(act_d), dptr<int64_t>(nqoff),
-                                             dptr<double>(nQ), dptr<double>(nT), nr);
+                                             dptr<double>(nQ), dptr<double>(nT), nr,
+                                             cin == 1 ? dptr<int>(nw_d) : nullptr);
       AMB_LAUNCHED();
     }
     project(Q, Q_OQ, cout * m, m);
@@ -1365,21 +1443,26 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   };
   auto rayleigh_ritz = [&](int w) {
     k_lob_gram_part<V><<<dim3(np, 2, ngchunk), 320, 0, st>>>(dptr<double>(Gpart), Q, QPd, m, w, dptr<int>(act_d),
-                                                            ngchunk);
+                                                            ngchunk, dptr<int>(nw_d));
     AMB_LAUNCHED();
     k_lob_gram_sum<<<dim3(np, 2), 256, 0, st>>>(dptr<double>(Gr), dptr<double>(Gpart), QPd, m, w, dptr<int>(act_d),
-                                               ngchunk);
+                                               ngchunk, dptr<int>(nw_d));
     AMB_LAUNCHED();
     const int wl = w + (w & 1);
     const size_t smem = (size_t)(5 * wl * wl + wl) * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_lob_rr<V><<<np, kJacobiThreads, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
-                                       svqb_drop);
+                                       svqb_drop, dptr<int>(nw_d));
     AMB_LAUNCHED();
     // [Xn Pn] = U [Cx | Cp] with Cp = Cx with the X rows zeroed, so
     // Pn = U(:, m:w) Cx(m:w, :) and Xn = U(:, 0:m) Cx(0:m, :) + Pn: two
     // products of N x m x (w-m) and N x m x m instead of N x 2m x w (the sum
     // is formed in the copy-back).  Same for AU and BU.
+    // Rows of the soft-locked W and P columns are zero in Cx.  The W and P
+    // parts stay one product (one accumulation chain per entry): splitting
+    // them into two products, the second adding into the first, changed the
+    // rounding of Pn enough to stall the pair of a stiff slab crossing the
+    // face (lambda_1 ~ 3e5) in the FP64 form.
     std::vector<GemmDesc> dp, dx;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
@@ -1441,6 +1524,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       int kuse = 0;
       while (kuse < m && kuse < maxad && hl[(size_t)p * m + kuse] > tau) ++kuse;
       kuse = std::min(m, kuse + 1);
+      nwh[p] = std::min(m, kuse + kGuard);
       double worst = 0.0;
       bool rising = false;
       for (int k = 0; k < kuse; ++k) {
@@ -1477,8 +1561,10 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     if (nact == 0) break;
     for (int p = 0; p < np; ++p) iters[p] += active[p];
     AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    AMB_CUDA(cudaMemcpyAsync(nw_d.p, nwh.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
     // R (W slot) -> temp panel columns 0..m, then W = M R
-    k_lob_copy_w<V><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<V>(Tp), Q, QPd, m, dptr<int>(act_d));
+    k_lob_copy_w<V><<<dim3(nblk(maxN * m), np), 256, 0, st>>>(dptr<V>(Tp), Q, QPd, m, dptr<int>(act_d),
+                                                             dptr<int>(nw_d));
     AMB_LAUNCHED();
     applyM(1);
     applyA(1, 4);

@@ -28,7 +28,10 @@ namespace {
 
 // Device address of the scratch array on the current device.  Host code
 // only knows a host-side stand-in for the symbol, so the real address is
-// queried once per device (with that device current) and cached.
+// queried once per device (with that device current) and cached for the
+// life of the process.  A device reset (cudaDeviceReset, or a reset of the
+// primary context) reloads the module and invalidates the cached address:
+// processes that reset a device must not call this entry point afterwards.
 void* scratch_address(int dev) {
   AMB_CHECK(dev >= 0 && dev < kMaxDevices, AMB_EINVAL, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(g_mu);
@@ -58,6 +61,12 @@ extern "C" int amb_schur_apply_noalloc(amb_ctx* c, int32_t level, int32_t width,
     int dev = -1;
     AMB_CUDA(cudaGetDevice(&dev));
     AMB_CHECK(dev == c->device, AMB_EINVAL, "the context's device must be current");
+    // the call copies its descriptors from host memory and waits for the
+    // stream: it cannot be recorded into a CUDA graph
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    AMB_CUDA(cudaStreamIsCapturing(c->st, &cs));
+    AMB_CHECK(cs == cudaStreamCaptureStatusNone, AMB_EINVAL,
+              "amb_schur_apply_noalloc called while the context stream is being captured");
     void* scratch = scratch_address(dev);
     c->eng->schur_apply_staged(level, width, x, y, scratch, kNoAllocScratchBytes);
     AMB_CUDA(cudaStreamSynchronize(c->st));
