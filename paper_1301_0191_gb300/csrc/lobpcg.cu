@@ -409,8 +409,10 @@ __global__ void k_lob_nullproj(double* base, const int64_t* qp, int cin, int cou
 // offset QP(p, which) (+ c0*N).  One warp per (group, column).
 template <typename T>
 __global__ void k_lob_project(T* base, const int64_t* qp, int which, int c0, int w, const int32_t* goff,
-                              const int32_t* gent, const double* gw, const int32_t* ps, const int32_t* pt) {
+                              const int32_t* gent, const double* gw, const int32_t* ps, const int32_t* pt,
+                              const int* act) {
   const int p = blockIdx.x;
+  if (!act[p]) return;
   const int64_t N = QP(p, Q_N), ns = QP(p, Q_NS);
   const int64_t g0 = QP(p, Q_GBEG), g1 = QP(p, Q_GEND), foff = QP(p, Q_FOFF);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -719,8 +721,8 @@ __global__ void k_lob_gram_sum(double* G, const double* part, const int64_t* qp,
 // Rayleigh-Ritz on the width-w basis: SVQB with column scaling, then the
 // reduced standard eigenproblem; coefficients Cc = [Cx | Cp] (3m x 2m, T)
 // and the m largest Ritz values.  Frozen pairs keep X (Cx = I, Cp = 0).
-template <typename T>
-__global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int wfull,
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, kJacobiThreads / NT) k_lob_rr(T* Cc, double* lam, const double* G, const int64_t* qp, const int* active, int m, int wfull,
                          double drop, const int* nwa) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
@@ -739,7 +741,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_lob_rr(T* Cc, double* lam, c
   double* Mr = V + ld * ld;
   double* Yr = Mr + ld * ld;
   double* dsc = Yr + ld * ld;   // w
-  __shared__ double red[kJacobiThreads], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
+  __shared__ double red[NT], cs_[kJacobiMax / 2 + 1], sn_[kJacobiMax / 2 + 1];
   __shared__ int P_[kJacobiMax / 2 + 1], Q_[kJacobiMax / 2 + 1], ord[kJacobiMax], ord2[kJacobiMax];
   __shared__ int rank_sh;
   T* C = Cc + QP(p, Q_OCC);
@@ -975,6 +977,9 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     return;
   }
   const int maxad = std::max(0, cfg.opt.max_adaptive_per_face);
+  int n_sms = 0, dev = 0;
+  AMB_CUDA(cudaGetDevice(&dev));
+  AMB_CUDA(cudaDeviceGetAttribute(&n_sms, cudaDevAttrMultiProcessorCount, dev));
   // block size: the rows the method may add, the indicator column and 4
   // guard columns that keep the last used column from converging slowly
   const int m = std::min(AMB_MAX_EIG, maxad + 1 + 4);
@@ -1236,7 +1241,8 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   // slot indices (column offsets in units of m): X 0, W 1, P 2, AX 3, AW 4, AP 5, BX 6, BW 7, BP 8
   auto project = [&](V* base, int which, int c0, int w) {
     k_lob_project<V><<<np, 256, 0, st>>>(base, QPd, which, c0, w, dptr<int32_t>(dgoff), dptr<int32_t>(dgent),
-                                         dptr<double>(dgw), dptr<int32_t>(dps), dptr<int32_t>(dpt));
+                                         dptr<double>(dgw), dptr<int32_t>(dps), dptr<int32_t>(dpt),
+                                         dptr<int>(act_d));
     AMB_LAUNCHED();
   };
   int64_t maxN = 0, maxnf = 0;
@@ -1450,32 +1456,54 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     AMB_LAUNCHED();
     const int wl = w + (w & 1);
     const size_t smem = (size_t)(5 * wl * wl + wl) * sizeof(double);
-    AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_lob_rr<V><<<np, kJacobiThreads, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd, dptr<int>(act_d), m, w,
-                                       svqb_drop, dptr<int>(nw_d));
+    // one 1024-thread CTA per pair while the pairs fit on the SMs at once
+    // (latency of one pair); with more pairs, two 512-thread CTAs per SM, so
+    // that one pair's barriers and FP64 latency overlap another's work
+    if (np <= n_sms) {
+      AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V, kJacobiThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      k_lob_rr<V, kJacobiThreads><<<np, kJacobiThreads, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr), QPd,
+                                                                   dptr<int>(act_d), m, w, svqb_drop, dptr<int>(nw_d));
+    } else {
+      AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V, kJacobiThreads / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      AMB_CUDA(cudaFuncSetAttribute(k_lob_rr<V, kJacobiThreads / 2>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    cudaSharedmemCarveoutMaxShared));
+      k_lob_rr<V, kJacobiThreads / 2><<<np, kJacobiThreads / 2, smem, st>>>(dptr<V>(Cc), dptr<double>(lam), dptr<double>(Gr),
+                                                                           QPd, dptr<int>(act_d), m, w, svqb_drop,
+                                                                           dptr<int>(nw_d));
+    }
     AMB_LAUNCHED();
     // [Xn Pn] = U [Cx | Cp] with Cp = Cx with the X rows zeroed, so
     // Pn = U(:, m:w) Cx(m:w, :) and Xn = U(:, 0:m) Cx(0:m, :) + Pn: two
     // products of N x m x (w-m) and N x m x m instead of N x 2m x w (the sum
     // is formed in the copy-back).  Same for AU and BU.
-    // Rows of the soft-locked W and P columns are zero in Cx.  The W and P
-    // parts stay one product (one accumulation chain per entry): splitting
-    // them into two products, the second adding into the first, changed the
-    // rounding of Pn enough to stall the pair of a stiff slab crossing the
-    // face (lambda_1 ~ 3e5) in the FP64 form.
-    std::vector<GemmDesc> dp, dx;
+    // Rows of the soft-locked W and P columns are zero in Cx.  The FP32 form
+    // multiplies only the active rows: Pn = W(:, 0:nw) Cx(W rows) and then
+    // += P(:, 0:nw) Cx(P rows).  The FP64 form (no soft locking) keeps the W
+    // and P parts in one product, one accumulation chain per entry, as the
+    // plain method.
+    std::vector<GemmDesc> dp, dpp, dx;
+    const bool split = sizeof(T) == sizeof(float) && w > 2 * m;
     for (int p = 0; p < np; ++p) {
       const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
       if (!active[p]) continue;
       const int64_t N = q[Q_N];
+      const int nwp = std::min(nwh[p], m);
       for (int g = 0; g < 3; ++g) {
         const int64_t u = q[Q_OQ] + (int64_t)3 * g * m * N, t = q[Q_OT] + (int64_t)2 * g * m * N;
-        dp.push_back(GemmDesc{(int)N, m, w - m, (int)N, m3, (int)N, u + (int64_t)m * N, q[Q_OCC] + m,
-                              t + (int64_t)m * N});
+        if (split) {
+          dp.push_back(GemmDesc{(int)N, m, nwp, (int)N, m3, (int)N, u + (int64_t)m * N, q[Q_OCC] + m,
+                                t + (int64_t)m * N});
+          dpp.push_back(GemmDesc{(int)N, m, nwp, (int)N, m3, (int)N, u + (int64_t)2 * m * N, q[Q_OCC] + 2 * m,
+                                 t + (int64_t)m * N});
+        } else {
+          dp.push_back(GemmDesc{(int)N, m, w - m, (int)N, m3, (int)N, u + (int64_t)m * N, q[Q_OCC] + m,
+                                t + (int64_t)m * N});
+        }
         dx.push_back(GemmDesc{(int)N, m, m, (int)N, m3, (int)N, u, q[Q_OCC], t});
       }
     }
     gemm_batched<V>(st, ring, dp, G_TUNE, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
+    if (!dpp.empty()) gemm_batched<V>(st, ring, dpp, 0, 1.0, 1.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     gemm_batched<V>(st, ring, dx, G_TUNE, 1.0, 0.0, Q, dptr<V>(Cc), dptr<V>(Tp));
     k_lob_copyback<V><<<dim3(nblk(maxN * 6 * m), np), 256, 0, st>>>(Q, dptr<V>(Tp), QPd, m, dptr<int>(act_d));
     AMB_LAUNCHED();

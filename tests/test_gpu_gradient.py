@@ -1,8 +1,11 @@
 """Adjoint gradient of the compliance on the 64^3 Poisson workload (4x4x4
 substructures, log-GRF coefficients), through the C ABI:
 
-- against central finite differences of Q = f^T u in 20 seeded directions,
-  1e-5 relative (each Q from its own set-up + solve at rtol 1e-12);
+- against central finite differences of Q = f^T u in 20 seeded directions
+  d ~ N(0, I) (not normalized: |d| ~ 512) with h = 1e-5, 1e-5 relative (each
+  Q from its own set-up + solve at rtol 1e-12).  With normalized directions
+  and h = 1e-6 the compliance moves by about 1e-11 of itself, next to the
+  solves' 1e-12, and the quotient's rounding error was 2e-3 (measured);
 - against the oracle's adjoint gradient at 512 seeded sample elements and its
   compliance (tests/golden/config4_gradient.json, written from oracle/ only).
   The gradient is quadratic in u, so the solution's 1e-6 relative bound
