@@ -161,9 +161,13 @@ class Level:
 
     # ---------------------------------------------------------------- Sec. 7.1
     def _initial_constraints(self):
-        """Sec. 7.1 corners + edge averages.  Pinned by
-        test_oracle_levels.py::test_coarse_basis_identities (C Psi = I) and
-        test_oracle_solver.py::test_all_corners_one_iteration."""
+        """Sec. 7.1 corners + edge averages ("ce"); corners only ("c"); or, for
+        the non-adaptive variant of Sec. 8.2 (Table 6, "c+e+f"), corners +
+        arithmetic averages over every edge and every face, per component
+        ("cef").  Pinned by test_oracle_levels.py::test_coarse_basis_identities
+        (C Psi = I), test_oracle_solver.py::test_all_corners_one_iteration and
+        test_oracle_face_averages.py (the face rows against the face nodes found
+        by brute force; more constraints cannot raise lambda_max(M A))."""
         self.objects: List[CoarseObject] = []
         for i in np.nonzero(self.node_corner)[0]:
             dofs = self.dofs_of_node[i]
@@ -172,20 +176,23 @@ class Level:
                 kind="corner", subs=self.node_subs[i], node=int(i), coord=coord,
                 dofs=[np.array([d]) for d in dofs], weights=[np.ones(1) for _ in dofs],
                 comps=[int(self.comp_of_dof[d]) for d in dofs]))
-        if self.initial in ("ce",):
-            for key in sorted(self.edges):
-                nodes = self.edges[key]
-                alld = np.concatenate([self.dofs_of_node[i] for i in nodes]).astype(np.int64)
-                comps = self.comp_of_dof[alld]
-                if np.any(comps < 0):
-                    raise ValueError("scalar coarse dofs on an edge")
-                dl, wl, cl = [], [], []
-                for c in sorted(set(comps.tolist())):
-                    dd = np.sort(alld[comps == c])
-                    dl.append(dd)
-                    wl.append(np.full(dd.size, 1.0 / dd.size))
-                    cl.append(int(c))
-                self.objects.append(CoarseObject(kind="edge", subs=key, dofs=dl, weights=wl, comps=cl))
+        groups = []
+        if self.initial in ("ce", "cef"):
+            groups += [("edge", key, self.edges[key]) for key in sorted(self.edges)]
+        if self.initial == "cef":
+            groups += [("face", key, self.faces[key]) for key in sorted(self.faces)]
+        for kind, key, nodes in groups:
+            alld = np.concatenate([self.dofs_of_node[i] for i in nodes]).astype(np.int64)
+            comps = self.comp_of_dof[alld]
+            if np.any(comps < 0):
+                raise ValueError(f"scalar coarse dofs on an {kind}")
+            dl, wl, cl = [], [], []
+            for c in sorted(set(comps.tolist())):
+                dd = np.sort(alld[comps == c])
+                dl.append(dd)
+                wl.append(np.full(dd.size, 1.0 / dd.size))
+                cl.append(int(c))
+            self.objects.append(CoarseObject(kind=kind, subs=key, dofs=dl, weights=wl, comps=cl))
         self._number_coarse()
 
     def _number_coarse(self):
