@@ -56,6 +56,8 @@ extern "C" {
 /* initial constraints (Sec. 7.1) */
 #define AMB_CORNERS        1   /* corners only */
 #define AMB_CORNERS_EDGES  2   /* corners + arithmetic edge averages (paper default) */
+#define AMB_CORNERS_EDGES_FACES 3 /* + arithmetic face averages, one per face and component: the
+                                     non-adaptive "c+e+f" of Sec. 8.2 (Table 6); requires adaptive = 0 */
 
 /* quantity of interest for amb_grad */
 #define AMB_QOI_COMPLIANCE 0   /* q = f^T u, adjoint = u */
@@ -93,7 +95,7 @@ typedef struct {
 
 typedef struct {
   int32_t precision;            /* AMB_FP64 | AMB_FP32 */
-  int32_t initial_constraints;  /* AMB_CORNERS | AMB_CORNERS_EDGES */
+  int32_t initial_constraints;  /* AMB_CORNERS | AMB_CORNERS_EDGES | AMB_CORNERS_EDGES_FACES */
   int32_t adaptive;             /* 1 = adaptive face constraints (Algorithm 3), 0 = initial constraints only */
   int32_t max_adaptive_per_face;/* at most this many rows per face (paper: 10) */
   int32_t lobpcg_maxit;         /* LOBPCG iteration cap (paper mode 15) */

@@ -16,7 +16,7 @@ from .build import LIB
 
 OK, EINVAL, ENOMEM, ENOTSPD, EASSUMPTION, ENOCONV, ETIMEOUT, ECUDA = range(8)
 FP64, FP32 = 0, 1
-CORNERS, CORNERS_EDGES = 1, 2
+CORNERS, CORNERS_EDGES, CORNERS_EDGES_FACES = 1, 2, 3
 QOI_COMPLIANCE, QOI_GENERAL = 0, 1
 MAX_EIG, MAX_LEVELS, FAM_N = 16, 8, 9
 X_SUB_DOFS, X_SUB_SIZES, X_SCHUR, X_COARSE_EL, X_CONSTR, X_CORNERS, X_PAIR_ROWS = range(1, 8)

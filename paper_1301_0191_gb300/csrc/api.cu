@@ -149,8 +149,11 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
     AMB_CHECK(levels >= 2 && levels <= AMB_MAX_LEVELS, AMB_EINVAL, "levels must be in [2, 8]");
     AMB_CHECK(tau > 0, AMB_EINVAL, "tau must be positive");
     AMB_CHECK(opt->precision == AMB_FP64 || opt->precision == AMB_FP32, AMB_EINVAL, "unknown precision");
-    AMB_CHECK(opt->initial_constraints == AMB_CORNERS || opt->initial_constraints == AMB_CORNERS_EDGES, AMB_EINVAL,
-              "unknown initial constraints");
+    AMB_CHECK(opt->initial_constraints == AMB_CORNERS || opt->initial_constraints == AMB_CORNERS_EDGES ||
+                  opt->initial_constraints == AMB_CORNERS_EDGES_FACES,
+              AMB_EINVAL, "unknown initial constraints");
+    AMB_CHECK(opt->initial_constraints != AMB_CORNERS_EDGES_FACES || opt->adaptive == 0, AMB_EINVAL,
+              "face averages are initial constraints of the non-adaptive method (c+e+f); set adaptive = 0");
     AMB_CHECK(opt->max_adaptive_per_face >= 0 && opt->max_adaptive_per_face < AMB_MAX_EIG, AMB_EINVAL,
               "max_adaptive_per_face must be in [0, 15]");
     AMB_CHECK(mesh->dirichlet_node_mask && part->elem_to_sub && coeffs->coeff, AMB_EINVAL, "NULL array");
@@ -426,8 +429,9 @@ int amb_plan(const amb_mesh* mesh, const amb_partition* part, int32_t levels, in
     AMB_CHECK(mesh->dofs_per_node == 1 || mesh->dofs_per_node == 3, AMB_EINVAL, "dofs_per_node must be 1 or 3");
     AMB_CHECK(levels >= 2 && levels <= AMB_MAX_LEVELS, AMB_EINVAL, "levels must be in [2, 8]");
     AMB_CHECK(level >= 1 && level <= levels - 1, AMB_EINVAL, "level out of range");
-    AMB_CHECK(initial_constraints == AMB_CORNERS || initial_constraints == AMB_CORNERS_EDGES, AMB_EINVAL,
-              "unknown initial constraints");
+    AMB_CHECK(initial_constraints == AMB_CORNERS || initial_constraints == AMB_CORNERS_EDGES ||
+                  initial_constraints == AMB_CORNERS_EDGES_FACES,
+              AMB_EINVAL, "unknown initial constraints");
     AMB_CHECK(mesh->dirichlet_node_mask && part->elem_to_sub, AMB_EINVAL, "NULL array");
     AMB_CHECK(part->n_sub1 >= 1, AMB_EINVAL, "n_sub1 must be >= 1");
     std::vector<int> nsubs{part->n_sub1};

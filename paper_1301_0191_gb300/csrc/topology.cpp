@@ -42,6 +42,33 @@ bool set_equal(const LevelNodes& N, int a, int b) {
   return N.nsub(a) == N.nsub(b) && std::equal(N.sub(a), N.sub(a) + N.nsub(a), N.sub(b));
 }
 
+// One arithmetic average per component over the dofs of `nodes` (an edge
+// or a face: nodes with the same sharing set), weights 1/n (Sec. 7.1).
+CoarseObj average_object(const LevelNodes& N, int kind, const std::vector<int>& nodes) {
+  CoarseObj ob;
+  ob.kind = kind;
+  ob.subs.assign(N.sub(nodes[0]), N.sub(nodes[0]) + N.nsub(nodes[0]));
+  int tags = ~0;
+  std::map<int, std::vector<int64_t>> bycomp;
+  for (int i : nodes) {
+    tags &= N.tags[i];
+    for (int64_t q = N.doff[i]; q < N.doff[i + 1]; ++q) {
+      AMB_CHECK(N.comps[q] >= 0, AMB_EINVAL,
+                kind == OBJ_EDGE ? "a scalar coarse dof lies on an edge of the next level"
+                                 : "a scalar coarse dof lies on a face of the next level");
+      bycomp[N.comps[q]].push_back(N.dofs[q]);
+    }
+  }
+  ob.tags = tags;
+  for (auto& c : bycomp) {
+    std::sort(c.second.begin(), c.second.end());
+    ob.comps.push_back(c.first);
+    ob.w.push_back(std::vector<double>(c.second.size(), 1.0 / (double)c.second.size()));
+    ob.dofs.push_back(c.second);
+  }
+  return ob;
+}
+
 // Classify the nodes of a level and build its substructures, objects and
 // interface numbering.
 void classify(LevelTopo& L, const LevelNodes& N, int initial) {
@@ -130,33 +157,15 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
       faces.emplace_back(i0, std::vector<int>(grp.begin() + r, grp.begin() + e));
     } else {
       ++L.n_edges;
-      if (initial == AMB_CORNERS_EDGES) {
-        CoarseObj ob;
-        ob.kind = OBJ_EDGE;
-        ob.subs.assign(N.sub(i0), N.sub(i0) + N.nsub(i0));
-        int tags = ~0;
-        std::map<int, std::vector<int64_t>> bycomp;
-        for (size_t g = r; g < e; ++g) {
-          const int i = grp[g];
-          tags &= N.tags[i];
-          for (int64_t q = N.doff[i]; q < N.doff[i + 1]; ++q) {
-            AMB_CHECK(N.comps[q] >= 0, AMB_EINVAL, "a scalar coarse dof lies on an edge of the next level");
-            bycomp[N.comps[q]].push_back(N.dofs[q]);
-          }
-        }
-        ob.tags = tags;
-        for (auto& c : bycomp) {
-          std::sort(c.second.begin(), c.second.end());
-          ob.comps.push_back(c.first);
-          ob.w.push_back(std::vector<double>(c.second.size(), 1.0 / (double)c.second.size()));
-          ob.dofs.push_back(c.second);
-        }
-        L.objs.push_back(std::move(ob));
-      }
+      if (initial == AMB_CORNERS_EDGES || initial == AMB_CORNERS_EDGES_FACES)
+        L.objs.push_back(average_object(N, OBJ_EDGE, std::vector<int>(grp.begin() + r, grp.begin() + e)));
     }
     r = e;
   }
   L.n_faces = (int)faces.size();
+  // face averages (Sec. 8.2, "c+e+f"), after the edges, in sharing-set order
+  if (initial == AMB_CORNERS_EDGES_FACES)
+    for (auto& f : faces) L.objs.push_back(average_object(N, OBJ_FACE, f.second));
 
   // substructure dof lists: interior, delta, corner (each sorted by level dof)
   L.subs.assign(L.n_subs, SubTopo());

@@ -21,10 +21,10 @@
 
 namespace amb {
 
-enum ObjKind { OBJ_CORNER = 0, OBJ_EDGE = 1, OBJ_ADAPTIVE = 2 };
+enum ObjKind { OBJ_CORNER = 0, OBJ_EDGE = 1, OBJ_ADAPTIVE = 2, OBJ_FACE = 3 };
 
-// A coarse object: a corner node (one coarse dof per component), an edge
-// (one arithmetic average per component) or one adaptive face row.
+// A coarse object: a corner node (one coarse dof per component), an edge or
+// a face (one arithmetic average per component) or one adaptive face row.
 struct CoarseObj {
   int kind = OBJ_CORNER;
   std::vector<int> subs;                      // sharing substructures (sorted)

@@ -27,13 +27,16 @@ def _cases():
     yield "irregular_elast", ai._make("irr3", 10, None, 3, np.ones(1000), 2, 10.0, cuts1=cuts)
 
 
-@pytest.mark.parametrize("initial", ["ce", "c"])
+def _initial(B, initial):
+    return {"c": B.CORNERS, "ce": B.CORNERS_EDGES, "cef": B.CORNERS_EDGES_FACES}[initial]
+
+
+@pytest.mark.parametrize("initial", ["ce", "c", "cef"])
 @pytest.mark.parametrize("name,prob", list(_cases()))
 def test_level_one_plan_matches_oracle(name, prob, initial):
     from paper_1301_0191_gb300 import binding as B
     info, subs = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
-                        prob.elem_to_sub, prob.n_subs(1),
-                        initial=B.CORNERS_EDGES if initial == "ce" else B.CORNERS)
+                        prob.elem_to_sub, prob.n_subs(1), initial=_initial(B, initial))
     lev = olv.level_one(prob, initial=initial)
     _compare(info, subs, lev, name)
 
@@ -73,20 +76,22 @@ def _multilevel_cases():
     yield "irregular_to_2x2x2", ai._make("irr", 16, None, 1, np.ones(16 ** 3), 3, 10.0, groups=g, cuts1=cuts)
 
 
+@pytest.mark.parametrize("initial", ["ce", "cef"])
 @pytest.mark.parametrize("name,prob", list(_multilevel_cases()))
-def test_level_two_plan_matches_oracle(name, prob):
+def test_level_two_plan_matches_oracle(name, prob, initial):
     """Level 2 of a non-adaptive three-level hierarchy: the nodes are the
-    level-1 corners and edges, only level-1 corners may become corners."""
+    level-1 corners, edges (and faces, with face averages), only level-1
+    corners may become corners."""
     from paper_1301_0191_gb300 import binding as B
-    h = solver.Hierarchy(prob, adaptive=False)
+    h = solver.Hierarchy(prob, adaptive=False, initial=initial)
     info, subs = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
                         prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
-                        n_sub=[prob.n_subs(2)], level=2)
+                        n_sub=[prob.n_subs(2)], level=2, initial=_initial(B, initial))
     _compare(info, subs, h.levels[1], name)
     # level 1 of the same hierarchy
     info1, subs1 = B.plan(prob.nx, prob.ny, prob.nz, prob.dofs_per_node, prob.dirichlet_node_mask,
                           prob.elem_to_sub, prob.n_subs(1), levels=3, sub_to_parent=prob.sub_to_parent,
-                          n_sub=[prob.n_subs(2)], level=1)
+                          n_sub=[prob.n_subs(2)], level=1, initial=_initial(B, initial))
     _compare(info1, subs1, h.levels[0], name)
 
 
