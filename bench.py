@@ -36,6 +36,9 @@ WORKLOAD = "elasticity48_4x4x4_lognormal"
 # the kernel has changed since)
 TC_TRAFFIC_PER_TILE = 1036088832 / 7240
 TC_OUTER, TC_TILE = 256, 128
+# DRAM bytes (read + write) of one B apply of the LOBPCG operator products on the 48^3 workload, from one
+# 1-pass ncu capture of the timed step (None when the kernel has changed since)
+TRAFFIC_GEMM_DF_B = 1.11e9 + 0.040e9
 
 
 def max_over_ranks(ms, world, device):
@@ -322,20 +325,27 @@ def main():
     if lop["ms"] > 0:
         ach = lop["flops"] / (lop["ms"] * 1e-3) / 1e12
         gbs = lop["bytes"] / (lop["ms"] * 1e-3) / 1e9
+        sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+        if fp == "fp32":
+            # FP32-pair multiply-adds: 11 FP32 instructions each (product split by an FMA, TwoSum, low word)
+            pair_peak = 152 * 128 * sm_mhz * 1e6 / 11 * 2 / 1e12
+            peak, peak_src = pair_peak, (f"derived FP32-pair multiply-add rate: 152 SMs x 128 FP32 lanes x "
+                                         f"{sm_mhz:g} MHz / 11 instructions per multiply-add x 2 flops")
+        else:
+            peak, peak_src = alu_peak, "nominal FP64 rate 1.25 TFLOP/s"
         roofline = {"kernel": "k_gemm_df: LOBPCG A and B products S X (factor-precision S, FP64 block, "
                               "FP32-pair accumulation on the SIMT units)",
-                    "bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
-                    "traffic": None,
-                    "traffic_note": "null: the ncu counters were taken before the last change of this kernel's "
-                                    "launch shapes",
+                    "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "frac_of_plain_fp32_simt": ach / alu_peak,
+                    "traffic": TRAFFIC_GEMM_DF_B if args.workload == "c2" and fp == "fp32" else None,
+                    "traffic_note": "DRAM bytes of one full B apply (all 144 pairs) from one ncu capture of the "
+                                    "timed step (1-pass dram__bytes_read.sum + write); the algorithmic bytes of "
+                                    "that apply (S of every substructure once) are 1.06e9",
                     "algorithmic_GB/s": gbs, "hbm_frac_algorithmic": gbs / peaks["hbm_gbs"],
                     "algorithmic_flops": lop["flops"], "algorithmic_bytes": lop["bytes"],
-                    "launches": lop["launches"], "ms": lop["ms"],
-                    "peak_source": "derived SIMT FP32 rate: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock "
-                                   f"{peaks.get('sm_max_mhz', 2070.0):g} MHz" if fp == "fp32" else
-                                   "nominal FP64 rate 1.25 TFLOP/s",
-                    "units": "flops = 2 per multiply-add of S X; each costs ~10 FP32 instructions in FP32 pairs, "
-                             "so frac <= ~0.2 at the issue limit"}
+                    "launches": lop["launches"], "ms": lop["ms"], "peak_source": peak_src,
+                    "units": "flops = 2 per multiply-add of S X, counted over the active columns; bytes = each "
+                             "substructure's S (B) and each pair side's face block (A) once per apply"}
     # the factorization's kernel: the tensor-core trailing update (FP32 form)
     tc = fams["tc_trailing"]
     if fp == "fp32" and tc["ms"] > 0:
