@@ -37,3 +37,19 @@ def compliance_and_gradient(prob, coeff=None):
     f = fe.load_vector(prob)
     u = spla.spsolve(a.tocsc(), f)
     return float(f @ u), element_gradient(prob, u, u, coeff)
+
+
+def linear_qoi_and_gradient(prob, w_free, coeff=None):
+    """A linear quantity of interest q = w^T u (w on the free dofs), by sparse
+    LU, and its adjoint gradient: A lambda = w (A is symmetric), then the
+    element formula above.
+
+    Pinned by test_oracle_gradient.py::test_linear_qoi_gradient_vs_central_fd.
+    """
+    coeff = prob.coeff if coeff is None else coeff
+    a = fe.assemble_global(prob, coeff).tocsc()
+    f = fe.load_vector(prob)
+    lu = spla.splu(a)
+    u = lu.solve(f)
+    lam = lu.solve(np.asarray(w_free, dtype=float))
+    return float(w_free @ u), element_gradient(prob, u, lam, coeff)
