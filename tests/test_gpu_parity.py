@@ -1,7 +1,8 @@
 """Parity of the CUDA path (through the C ABI) with the CPU FP64 oracle.
 
 Tolerances (FP64 path): Schur complements and coarse matrices 1e-9
-relative to their norm; solution 1e-6 relative to a sparse direct solve at
+relative to their largest entry, entry by entry (coarse matrices after
+matching the constraint rows one to one); solution 1e-6 relative to a sparse direct solve at
 the 1e-8 PCG tolerance; pair eigenvalues above tau/10 within 1e-4
 relative (LOBPCG residual 1e-8); PCG iterations and selected constraint
 counts within +-1 (several results are correct at ties, Sec. 4).
@@ -68,6 +69,15 @@ def test_schur_and_coarse_matrices(B, dpn, split, seed):
         # same row space (constraint functionals), in the library's interface order
         Co = sb.c[:, perm]
         assert np.linalg.matrix_rank(np.vstack([Cl, Co]), tol=1e-10) == nc
+        # the initial constraints are unique functionals (corner dofs, edge
+        # averages): match the rows one to one, then A_c entry by entry
+        cperm = []
+        for row in Cl:
+            hit = np.nonzero(np.abs(Co - row).max(axis=1) <= 1e-12)[0]
+            assert hit.size == 1
+            cperm.append(int(hit[0]))
+        Aco = sb.ac[np.ix_(cperm, cperm)]
+        assert np.abs(Ac - Aco).max() <= 1e-9 * np.abs(Aco).max()
     ctx.close()
 
 
