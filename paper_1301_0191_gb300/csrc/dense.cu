@@ -989,24 +989,27 @@ void partial_cholesky(cudaStream_t st, DescRing& ring, const std::vector<CholDes
       if (flops) *flops += (double)rem * (rem + 1) * (J1 - J0);
     }
     if (trail.empty()) continue;
-    if constexpr (std::is_same<T, float>::value) {
-      // FP32 form: tensor cores (3xTF32, FP32 accuracy)
-      std::vector<TcSyrk> tc;
-      tc.reserve(trail.size());
-      double tfl = 0.0;
-      for (const auto& g : trail) {
-        tc.push_back(TcSyrk{g.a, g.c, g.lda, g.m, g.k, 0});
-        tfl += (double)g.m * (g.m + 1) * g.k;
-      }
-      if (tm) {
-        FamTimer ft(st, tm, AMB_FAM_TC, timing);
+    // on the tensor cores: 3xTF32 (FP32 accuracy) in the FP32 form, exact
+    // slice products (FP64 accuracy) in the FP64 form
+    std::vector<TcSyrk> tc;
+    tc.reserve(trail.size());
+    double tfl = 0.0;
+    for (const auto& g : trail) {
+      tc.push_back(TcSyrk{g.a, g.c, g.lda, g.m, g.k, 0});
+      tfl += (double)g.m * (g.m + 1) * g.k;
+    }
+    auto run = [&] {
+      if constexpr (std::is_same<T, float>::value)
         tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
-        tm->fam_flops[AMB_FAM_TC] += tfl;
-      } else {
-        tc_syrk_lower(st, ring, tc, -1.f, 1.f, base, status);
-      }
+      else
+        tc_syrk_lower_f64(st, ring, tc, -1.0, 1.0, base, status);
+    };
+    if (tm) {
+      FamTimer ft(st, tm, AMB_FAM_TC, timing);
+      run();
+      tm->fam_flops[AMB_FAM_TC] += tfl;
     } else {
-      gemm_batched<T>(st, ring, trail, G_TRANS_B | G_OUT_LOWER, T(-1), T(1), base, base, base);
+      run();
     }
   }
 }

@@ -287,14 +287,17 @@ __device__ void sort_desc(const double* A, int n, int ld, int* ord) {
 // annihilates the rigid modes restricted to its interface (constants for the
 // scalar problem; three translations and three rotations for elasticity),
 // exactly (Sec. 2: S is the energy of the discrete harmonic extension).  The
-// FP32 form's S, rounded through the FP32 factorization, gives these modes
-// an energy of about 1e-7 of its norm, and the pair denominator B = Pi S Pi
-// (eq. eig-matrix) is nearly singular exactly there: the pencils' large
-// eigenvalues then move by per cents and LOBPCG stalls on the pairs of two
-// floating substructures.  The FP32 form therefore applies B with
-// P S P, P = I - Q Q^T the orthogonal projector off the modes (Q orthonormal):
-// P S P x = S x - T a - Q b with a = Q^T x, T = S Q, b = Q^T (S x - T a),
-// in FP64 after the product.  For the exact S, P S P = S.
+// rounded S gives these modes an energy of the order of the factorization's
+// rounding (about 1e-7 of its norm in the FP32 form), and the pair
+// denominator B = Pi S Pi (eq. eig-matrix) is nearly singular exactly there:
+// the pencils' large eigenvalues then move by per cents and LOBPCG stalls on
+// the pairs of two floating substructures.  In the FP64 form the same
+// happens on stiff inclusions, where the pencils' eigenvalues reach 1e6 and
+// the spurious directions win by chance of rounding.  Both forms therefore
+// apply B with P S P, P = I - Q Q^T the orthogonal projector off the modes
+// (Q orthonormal): P S P x = S x - T a - Q b with a = Q^T x, T = S Q,
+// b = Q^T (S x - T a), in FP64 after the product.  For the exact S,
+// P S P = S.
 
 // Q (n_g x r per floating substructure, column-major) <- orthonormal basis of
 // its columns, two passes of classical Gram-Schmidt in FP64; one CTA each.
@@ -1150,13 +1153,13 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     }
     AMB_CUDA(cudaStreamSynchronize(st));   // keep the offset table alive until the kernel ran
   }
-  // FP32 form, level 1: rigid modes of the floating substructures (those
-  // whose elements touch no Dirichlet node), orthonormalized, and T = S Q
-  // with the same extended-precision product as the B applies
+  // level 1: rigid modes of the floating substructures (those whose elements
+  // touch no Dirichlet node), orthonormalized, and T = S Q with the same
+  // product as the B applies
   DevBuf nQ, nT, nqoff;
   int nr = 0;
   bool nullproj = false;
-  if (sizeof(T) == sizeof(float) && lvl == 1) {
+  if (lvl == 1) {
     const int dpn = mesh.dpn;
     nr = dpn == 1 ? 1 : 6;
     std::vector<uint8_t> touched(L.ns, 0);

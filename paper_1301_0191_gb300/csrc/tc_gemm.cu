@@ -372,6 +372,322 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(kAccCols) : "memory");
 }
 
+// ---------------------------------------------------------------- FP64 form: exact slice products
+//
+// C(lower) += alpha P P^T in FP64 accuracy on the TF32 tensor cores.  Row r of
+// P (one trailing-update panel, K <= 256) is scaled by 2^-e_r, e_r the
+// exponent of its largest entry, and cut into kOzSlices integer slices:
+// v = P(r, k) 2^-e_r in (-1, 1); t = 128 v, m_0 = rint(t), v = t - m_0; and
+// so on, so P(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-56 of the row's
+// largest entry, |m_0| <= 128, |m_p| <= 64.  These small integers are exact
+// in TF32 and so are their products; the products of slices p and q with
+// p + q = l go to TMEM accumulator l.  Per K-step a level collects at most
+// 2^14 + (l - 1) 2^12 (l >= 1) or 2^14 (l = 0), so over K = 256 every
+// partial sum is an integer below 10 * 2^20 < 2^24: exact in the FP32
+// accumulator whatever its rounding mode.  Products with p + q >= kOzSlices
+// are dropped (below 2^-49 of 2^(e_i + e_j)).  The epilogue adds the levels
+// times 2^-7(l+2) in FP32 pairs, smallest first (about 48 bits), and updates
+// C in FP64 with the factor 2^(e_i + e_j).
+//
+// Tiles are 128 x 64 (M x N): the eight accumulators of a tile fill the 512
+// TMEM columns.  Per K step of 32 the B rows of all slices (8 x 8 KB) sit in
+// one of two B buffers, and the A rows of one slice at a time (16 KB) in one
+// of three A stages: each slice tile is read from L2 once per K step.
+
+constexpr int kOzTN = 64, kOzBBufs = 2, kOzAStages = 3;
+constexpr int kOzATile = kTM * kTK * 4;                     // 16 KB
+constexpr int kOzBTile = kOzTN * kTK * 4;                   // 8 KB
+constexpr int kOzBBytes = kOzSlices * kOzBTile;             // 64 KB
+constexpr int kOzSmemBytes = kOzBBufs * kOzBBytes + kOzAStages * kOzATile + 1024;
+constexpr uint32_t kOzIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kOzTN >> 3) << 17) |
+                              ((uint32_t)(kTM >> 4) << 24);
+static_assert(kOzSlices * kOzTN <= 512, "the level accumulators must fit TMEM");
+static_assert(kOzSmemBytes <= 227 * 1024, "shared memory");
+
+__device__ __forceinline__ void mma_tf32_n64(uint32_t tacc, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
+      "l"(a), "l"(b), "r"(kOzIdesc), "r"(accumulate)
+      : "memory");
+}
+
+// (H 2^28 + L) 2^s rounded to the nearest double (ties to even), from the exact
+// 128-bit integer: one rounding however the two parts cancel
+__device__ __forceinline__ double oz_round(int64_t H, int64_t L, int s) {
+  const __int128 t = ((__int128)H << 28) + (__int128)L;
+  if (t == 0) return 0.0;
+  const bool neg = t < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const uint64_t uh = (uint64_t)(u >> 64), ul = (uint64_t)u;
+  int nb = uh ? 128 - __clzll((long long)uh) : 64 - __clzll((long long)ul);   // bit length
+  uint64_t m;
+  if (nb <= 53) {
+    m = ul << (53 - nb);
+  } else {
+    const int sh = nb - 53;
+    m = (uint64_t)(u >> sh);
+    const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1), half = (unsigned __int128)1 << (sh - 1);
+    if (rem > half || (rem == half && (m & 1))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++nb;
+    }
+  }
+  const int E = nb - 1 + s;   // exponent of the result
+  if (E < -1022 || E > 1023) return ldexp(neg ? -(double)m : (double)m, E - 52);
+  const uint64_t bits = ((uint64_t)(E + 1023) << 52) | (m & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull);
+  return __longlong_as_double((long long)bits);
+}
+
+// source rows x cols (column form: (r, k) at src + r + k * ld) -> slab rows
+// row0 .. row0 + rpad of every slice (slice p at slab row p * R + row), K
+// contiguous with stride kp; rows and columns outside the block are zero.
+// One thread per row: the reads along k are coalesced across the warp.
+__global__ void __launch_bounds__(128) k_oz_split(const TcSplitDesc* d, int kp, int64_t R, float* slab, int* ex) {
+  const TcSplitDesc x = d[blockIdx.y];
+  const int r = blockIdx.x * 128 + threadIdx.x;
+  if (r >= x.rpad) return;
+  const double* src = reinterpret_cast<const double*>(x.src);
+  const bool in = r < x.rows;
+  double mx = 0.0;
+  if (in)
+    for (int k = 0; k < x.cols; ++k) mx = fmax(mx, fabs(src[r + (int64_t)k * x.ld]));
+  int e = 0;
+  if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |P(r, k)| 2^-e < 1
+  ex[x.row0 + r] = e;
+  for (int k0 = 0; k0 < kp; k0 += 4) {
+    float sl[kOzSlices][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u;
+      double v = (in && k < x.cols) ? ldexp(src[r + (int64_t)k * x.ld], -e) : 0.0;
+#pragma unroll
+      for (int p = 0; p < kOzSlices; ++p) {
+        const double t = v * 128.0;
+        const double m = rint(t);
+        v = t - m;
+        sl[p][u] = (float)m;
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < kOzSlices; ++p)
+      *reinterpret_cast<float4*>(slab + (p * R + x.row0 + r) * (int64_t)kp + k0) =
+          make_float4(sl[p][0], sl[p][1], sl[p][2], sl[p][3]);
+  }
+}
+
+// tile t of a lower 128 x 64 tiling of an m x m matrix: row tile ti has
+// min(2 ti + 2, tn) column tiles
+__device__ __forceinline__ void oz_tile(const TcTileArgs& g, int tile, TcDesc& d, int& ti, int& tj) {
+  int lo = 0, hi = g.ndesc - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (g.prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  d = g.desc[lo];
+  const int t = tile - g.prefix[lo];
+  ti = (int)((sqrtf(4.f * t + 1.f) - 1.f) * 0.5f);
+  while (ti * (ti + 1) > t) --ti;
+  while ((ti + 1) * (ti + 2) <= t) ++ti;
+  tj = t - ti * (ti + 1);
+}
+
+struct OzArgs {
+  const TcDesc* desc;
+  const int* prefix;
+  int ndesc;
+  int64_t R;
+  double alpha, beta;
+  double* c;
+  const int* ex;
+  int* status;
+};
+
+__global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUtensorMap map_a,
+                                                   const __grid_constant__ CUtensorMap map_b, OzArgs ga) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t bfull[kOzBBufs], bempty[kOzBBufs], afull[kOzAStages], aempty[kOzAStages], tfull,
+      tempty;
+  __shared__ uint32_t tbase;
+  __shared__ volatile int abort_sh;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  TcTileArgs g;
+  g.desc = ga.desc;
+  g.prefix = ga.prefix;
+  g.ndesc = ga.ndesc;
+  g.status = ga.status;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)), "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < kOzBBufs; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bfull[s])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bempty[s])), "r"(1) : "memory");
+    }
+    for (int s = 0; s < kOzAStages; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[s])), "r"(1) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&aempty[s])), "r"(1) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfull)), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty)), "r"(4) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_a) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_b) : "memory");
+    abort_sh = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tacc = tbase;
+  const int ntiles = g.prefix[g.ndesc];
+  const int64_t R = ga.R;
+
+  uint8_t* const bbuf = smem;
+  uint8_t* const abuf = smem + kOzBBufs * kOzBBytes;
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      uint32_t ib = 0, ia = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x) {
+        TcDesc d;
+        int ti, tj;
+        oz_tile(g, tile, d, ti, tj);
+        const int64_t ya = d.arow + (int64_t)ti * kTM, yb = d.brow + (int64_t)tj * kOzTN;
+        const int nk = d.k / kTK;
+        bool ok = true;
+        for (int kt = 0; kt < nk && ok; ++kt, ++ib) {
+          const int sb = ib % kOzBBufs;
+          if (!role_wait(smem_u32(&bempty[sb]), ((ib / kOzBBufs) & 1) ^ 1, &abort_sh, g.status)) break;
+          const uint32_t bdst = smem_u32(bbuf + sb * kOzBBytes), bfb = smem_u32(&bfull[sb]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bfb), "r"(kOzBBytes) : "memory");
+          for (int q = 0; q < kOzSlices; ++q) tma_load_2d(bdst + q * kOzBTile, &map_b, kt * kTK, (int)(q * R + yb), bfb);
+          for (int p = 0; p < kOzSlices; ++p, ++ia) {
+            const int sa = ia % kOzAStages;
+            if (!role_wait(smem_u32(&aempty[sa]), ((ia / kOzAStages) & 1) ^ 1, &abort_sh, g.status)) {
+              ok = false;
+              break;
+            }
+            const uint32_t afb = smem_u32(&afull[sa]);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(afb), "r"(kOzATile) : "memory");
+            tma_load_2d(smem_u32(abuf + sa * kOzATile), &map_a, kt * kTK, (int)(p * R + ya), afb);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t ib = 0, ia = 0, tl = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x, ++tl) {
+        TcDesc d;
+        int ti, tj;
+        oz_tile(g, tile, d, ti, tj);
+        const int nk = d.k / kTK;
+        if (!role_wait(smem_u32(&tempty), (tl & 1) ^ 1, &abort_sh, g.status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool ok = true;
+        for (int kt = 0; kt < nk && ok; ++kt, ++ib) {
+          const int sb = ib % kOzBBufs;
+          if (!role_wait(smem_u32(&bfull[sb]), (ib / kOzBBufs) & 1, &abort_sh, g.status)) break;
+          const uint32_t bsrc = smem_u32(bbuf + sb * kOzBBytes);
+          for (int p = 0; p < kOzSlices; ++p, ++ia) {
+            const int sa = ia % kOzAStages;
+            if (!role_wait(smem_u32(&afull[sa]), (ia / kOzAStages) & 1, &abort_sh, g.status)) {
+              ok = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t asrc = smem_u32(abuf + sa * kOzATile);
+#pragma unroll
+            for (int kk = 0; kk < kTK / 8; ++kk) {
+              const uint32_t ko = kk * 32;   // K = 8 per MMA: 32 bytes along the swizzled row
+              const uint64_t da = smem_desc_sw128(asrc + ko);
+              // the first product into each level starts it: level l first sees (p, q) = (0, l)
+              for (int q = 0; q < kOzSlices - p; ++q)
+                mma_tf32_n64(tacc + (uint32_t)((p + q) * kOzTN), da, smem_desc_sw128(bsrc + q * kOzBTile + ko),
+                             (kt > 0 || p > 0 || kk > 0) ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&aempty[sa]))
+                         : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&bempty[sb]))
+                       : "memory");
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&tfull))
+                     : "memory");
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 2..5)
+    const int quad = warp & 3;   // TMEM lanes 32*quad .. 32*quad + 31
+    uint32_t tl = 0;
+    for (int tile = blockIdx.x; tile < ntiles && !abort_sh; tile += gridDim.x, ++tl) {
+      TcDesc d;
+      int ti, tj;
+      oz_tile(g, tile, d, ti, tj);
+      if (!role_wait(smem_u32(&tfull), tl & 1, &abort_sh, g.status)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
+      const bool row_ok = i < d.m;
+      const int ei = ga.ex[d.arow + min(i, d.m - 1)];
+      double* const crow = ga.c + d.c + i;
+#pragma unroll 1
+      for (int h = 0; h < kOzTN / 16; ++h) {
+        // levels 0..3 -> H, levels 4..7 -> L: the product is (H 2^28 + L) 2^-63
+        // in units of 2^(e_i + e_j), both parts exact in int64 (below 2^46)
+        int64_t part[2][16];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint32_t r[4][16];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const uint32_t ta =
+                tacc + ((uint32_t)(quad * 32) << 16) + (uint32_t)((half * 4 + a) * kOzTN + h * 16);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[a][0]), "=r"(r[a][1]), "=r"(r[a][2]), "=r"(r[a][3]), "=r"(r[a][4]), "=r"(r[a][5]),
+                  "=r"(r[a][6]), "=r"(r[a][7]), "=r"(r[a][8]), "=r"(r[a][9]), "=r"(r[a][10]), "=r"(r[a][11]),
+                  "=r"(r[a][12]), "=r"(r[a][13]), "=r"(r[a][14]), "=r"(r[a][15])
+                : "r"(ta));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            int64_t v = 0;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) v = v * 128 + (int64_t)__float2int_rn(__uint_as_float(r[a][q]));
+            part[half][q] = v;
+          }
+        }
+        if (row_ok) {
+          const int j0 = tj * kOzTN + h * 16;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int j = j0 + q;
+            if (j < d.n && j <= i) {
+              const double v = oz_round(part[0][q], part[1][q], ei + ga.ex[d.brow + j] - 63);
+              double* cp = crow + (int64_t)j * d.ldc;
+              *cp = ga.beta == 1.0 ? fma(ga.alpha, v, *cp) : fma(ga.alpha, v, ga.beta * *cp);
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty)) : "memory");
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tacc), "r"(512) : "memory");
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -388,12 +704,12 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// 2-D map over a slab (rows x kp FP32, row-major) with 128 x 32 boxes, 128-byte swizzle
-CUtensorMap slab_map(float* base, int64_t rows, int kp) {
+// 2-D map over a slab (rows x kp FP32, row-major) with box_rows x 32 boxes, 128-byte swizzle
+CUtensorMap slab_map(float* base, int64_t rows, int kp, int box_rows = kTM) {
   CUtensorMap m;
   const cuuint64_t dim[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   const cuuint64_t stride[1] = {(cuuint64_t)kp * sizeof(float)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)kTM}, estr[2] = {1, 1};
+  const cuuint32_t box[2] = {(cuuint32_t)kTK, (cuuint32_t)box_rows}, estr[2] = {1, 1};
   const CUresult r = encode_tiled()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dim, stride, box, estr,
                                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -499,6 +815,76 @@ void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d
   }
   if (td.empty()) return;
   run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, base, status);
+}
+
+void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
+                       double* base, int* status) {
+  if (d.empty()) return;
+  constexpr int kp = kTcKMax;
+  std::vector<TcSplitDesc> sp;
+  std::vector<TcDesc> td;
+  std::vector<int> prefix;
+  int64_t rows = 0, tiles = 0;
+  int maxr = 0;
+  for (const auto& x : d) {
+    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
+    if (x.rem <= 0 || x.k <= 0) continue;
+    const int rpad = pad_rows(x.rem);
+    // the split pass reads the FP64 source through the descriptor's pointer
+    sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(base + x.p), rows, x.ld, x.rem, x.k, rpad, 0, 0, 0, 0});
+    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0, 0, 1};
+    prefix.push_back((int)tiles);
+    const int tm = (x.rem + kTM - 1) / kTM, tn = (x.rem + kOzTN - 1) / kOzTN;
+    tiles += tm * (tm + 1) - (2 * tm - tn);   // row tile ti holds min(2 ti + 2, tn) column tiles
+    td.push_back(t);
+    rows += rpad;
+    maxr = std::max(maxr, rpad);
+  }
+  if (td.empty()) return;
+  AMB_CHECK(tiles < (1LL << 31) && rows * kOzSlices < (1LL << 31) && sp.size() < 65536, AMB_EINVAL,
+            "tensor-core batch too large");
+  static thread_local bool attr = false;
+  if (!attr) {
+    AMB_CUDA(cudaFuncSetAttribute(k_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemBytes));
+    attr = true;
+  }
+  static thread_local DevBuf slab_buf, ex_buf;
+  const size_t need = (size_t)kOzSlices * rows * kp * sizeof(float);
+  if (slab_buf.bytes < need || ex_buf.bytes < (size_t)rows * sizeof(int)) {
+    AMB_CUDA(cudaDeviceSynchronize());   // earlier launches may still read the old slab
+    if (slab_buf.bytes < need) slab_buf.alloc(need);
+    if (ex_buf.bytes < (size_t)rows * sizeof(int)) ex_buf.alloc((size_t)rows * sizeof(int));
+  }
+  float* slab = dptr<float>(slab_buf);
+  int* ex = dptr<int>(ex_buf);
+  prefix.push_back((int)tiles);
+  const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(sp.data(), sp.size() * sizeof(TcSplitDesc), st));
+  k_oz_split<<<dim3((unsigned)(maxr / 128), (unsigned)sp.size()), 128, 0, st>>>(dsp, kp, rows, slab, ex);
+  AMB_LAUNCHED();
+  std::vector<char> blob(td.size() * sizeof(TcDesc) + prefix.size() * sizeof(int));
+  memcpy(blob.data(), td.data(), td.size() * sizeof(TcDesc));
+  memcpy(blob.data() + td.size() * sizeof(TcDesc), prefix.data(), prefix.size() * sizeof(int));
+  char* dev = static_cast<char*>(ring.push(blob.data(), blob.size(), st));
+  OzArgs ga;
+  ga.desc = reinterpret_cast<const TcDesc*>(dev);
+  ga.prefix = reinterpret_cast<const int*>(dev + td.size() * sizeof(TcDesc));
+  ga.ndesc = (int)td.size();
+  ga.R = rows;
+  ga.alpha = alpha;
+  ga.beta = beta;
+  ga.c = base;
+  ga.ex = ex;
+  ga.status = status;
+  static thread_local int nsm = 0;
+  if (nsm == 0) {
+    int devid = 0;
+    AMB_CUDA(cudaGetDevice(&devid));
+    AMB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, devid));
+  }
+  const CUtensorMap ma = slab_map(slab, rows * kOzSlices, kp, kTM), mb = slab_map(slab, rows * kOzSlices, kp, kOzTN);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
+  k_oz_syrk<<<grid, 192, kOzSmemBytes, st>>>(ma, mb, ga);
+  AMB_LAUNCHED();
 }
 
 void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,

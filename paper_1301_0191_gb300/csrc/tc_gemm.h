@@ -66,4 +66,15 @@ void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d
 void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,
              const float* abase, const float* bbase, float* cbase, int* status);
 
+// FP64 form: C(lower) = beta C + alpha P P^T for every entry of d (FP64 data in
+// base) on the tensor cores, with FP64 accuracy from exact slice products:
+// every row of P is scaled by a power of two to |P(r, :)| < 1 and cut into
+// kOzSlices integer slices of 7 bits (exact in TF32); the products of slices
+// p and q with p + q < kOzSlices are summed per level p + q in FP32 TMEM
+// accumulators, where every partial sum is an integer below 2^24 and hence
+// exact; the levels are combined in FP32 pairs and added to C in FP64.
+constexpr int kOzSlices = 8;
+void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
+                       double* base, int* status);
+
 }  // namespace amb
