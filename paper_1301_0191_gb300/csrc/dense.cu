@@ -1033,9 +1033,10 @@ void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriD
     const int b = 2 * half;
     std::vector<GemmDesc> sa, sb;
     std::vector<TcGemm> ta, tb;
-    // FP32 form: merges with K >= the tensor-core chunk width run as 3xTF32
-    // tensor-core products (K in chunks, accumulated in FP32 through C)
-    const bool tc = std::is_same<T, float>::value && half >= kTcKMax;
+    // on the tensor cores: FP32-form merges with K >= the chunk width as 3xTF32
+    // products (K in chunks, accumulated in FP32 through C), every FP64-form
+    // merge from exact slice products (K in chunks, accumulated in FP64)
+    const bool tc = std::is_same<T, float>::value ? half >= kTcKMax : true;
     for (const auto& x : d) {
       for (int p0 = 0; p0 + half < x.n; p0 += b) {
         const int h = p0 + half;
@@ -1059,13 +1060,16 @@ void trtri_from_blocks(cudaStream_t st, DescRing& ring, const std::vector<TrtriD
         if (flops) *flops += (double)c1 * c1 * r2 + (double)r2 * r2 * c1;
       }
     }
-    if constexpr (std::is_same<T, float>::value) {
-      if (tc) {
-        if (ta.empty()) continue;
+    if (tc) {
+      if (ta.empty()) continue;
+      if constexpr (std::is_same<T, float>::value) {
         tc_gemm(st, ring, ta, 1.f, 0.f, zbase, lbase, zbase, status);
         tc_gemm(st, ring, tb, -1.f, 0.f, zbase, zbase, zbase, status);
-        continue;
+      } else {
+        tc_gemm_f64(st, ring, ta, 1.0, 0.0, zbase, lbase, zbase, status);
+        tc_gemm_f64(st, ring, tb, -1.0, 0.0, zbase, zbase, zbase, status);
       }
+      continue;
     }
     if (sa.empty()) continue;
     gemm_batched<T>(st, ring, sa, G_TRANS_A | G_TRI_A_UPPER | G_TRANS_B | G_TUNE, T(1), T(0), zbase, lbase, zbase);

@@ -408,6 +408,44 @@ __global__ void k_lob_nullproj(double* base, const int64_t* qp, int cin, int cou
   }
 }
 
+// x <- x - Q (Q^T x) on the leading columns of one slot of the FP64 panel,
+// for the pairs with a deflation basis Q (N x r, orthonormal, at Qp +
+// qoff[p]; qoff[p] < 0: none).  One CTA per pair, one warp per column
+// (fixed-order lane sums and shuffles: deterministic).  ncol: per pair, the
+// number of leading columns that can be nonzero (nullptr: all m).
+__global__ void k_lob_deflate(double* base, const int64_t* qp, int slot, int m, const int* act, const int64_t* qoff,
+                              const double* Qp, int r, const int* ncol) {
+  const int p = blockIdx.x;
+  if (!act[p]) return;
+  const int64_t o = qoff[p];
+  if (o < 0) return;
+  const int64_t N = QP(p, Q_N);
+  const double* Qs = Qp + o;
+  double* x = base + QP(p, Q_OQ) + (int64_t)slot * m * N;
+  const int nc = ncol ? min(ncol[p], m) : m;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nwarp) {
+    double* xc = x + (int64_t)c * N;
+    double a[6] = {0, 0, 0, 0, 0, 0};
+    for (int64_t i = lane; i < N; i += 32) {
+      const double xv = xc[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) a[k] = fma(Qs[(int64_t)k * N + i], xv, a[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      for (int off = 16; off > 0; off >>= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+    for (int64_t i = lane; i < N; i += 32) {
+      double v = xc[i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (k < r) v = fma(-Qs[(int64_t)k * N + i], a[k], v);
+      xc[i] = v;
+    }
+  }
+}
+
 // Pi on columns [c0, c0+w) of a block with leading dimension N at base
 // offset QP(p, which) (+ c0*N).  One warp per (group, column).
 template <typename T>
@@ -580,7 +618,7 @@ __global__ void k_lob_cscatter(T* C, const int64_t* qp, int m, const int32_t* cm
 // eigen-decomposition, eigenvalues below a tolerance dropped)
 template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads) k_pair_pinv(T* pinv, const int64_t* qp, const double* Ac, const int64_t* acs, const int64_t* act,
-                            const int32_t* cms, const int32_t* cmt, int* status) {
+                            const int32_t* cms, const int32_t* cmt, const int* nnull, int* status) {
   extern __shared__ double sh[];
   const int p = blockIdx.x;
   const int n = (int)QP(p, Q_NCP), ncs = (int)QP(p, Q_NCS), nct = (int)QP(p, Q_NCT);
@@ -605,7 +643,37 @@ __global__ void __launch_bounds__(kJacobiThreads) k_pair_pinv(T* pinv, const int
   jacobi_eig(A, V, n, ld, red, cs_, sn_, P_, Q_);
   double mx = 0.0;
   for (int i = 0; i < n; ++i) mx = fmax(mx, A[i + i * ld]);
-  const double tol = 1e-12 * mx;
+  // a floating pair's coarse matrix annihilates the coarse values of the
+  // pair's rigid modes exactly; its computed eigenvalues there are rounding
+  // (which the relative cut below can keep), and their inverses would blow
+  // the rigid directions up by the inverse of that rounding: the nnull[p]
+  // smallest eigenvalues are left out, as the pseudo-inverse of the exact
+  // matrix leaves out its null space
+  __shared__ double cut_sh;
+  if (threadIdx.x == 0) {
+    double cut = 1e-12 * mx;
+    const int k = min(nnull ? nnull[p] : 0, n);
+    if (k > 0) {
+      // the k-th smallest eigenvalue, by repeated minimum
+      double last = -1e300;
+      int taken = 0;
+      while (taken < k) {
+        double mn = 1e300;
+        int cnt = 0;
+        for (int i = 0; i < n; ++i) {
+          const double l = A[i + i * ld];
+          if (l > last && l < mn) mn = l, cnt = 0;
+          if (l == mn) ++cnt;
+        }
+        last = mn;
+        taken += max(cnt, 1);
+      }
+      cut = fmax(cut, last);
+    }
+    cut_sh = cut;
+  }
+  __syncthreads();
+  const double tol = cut_sh;
   T* out = pinv + QP(p, Q_OPI);
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     int r = idx % n, c = idx / n;
@@ -1155,10 +1223,16 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   }
   // level 1: rigid modes of the floating substructures (those whose elements
   // touch no Dirichlet node), orthonormalized, and T = S Q with the same
-  // product as the B applies
-  DevBuf nQ, nT, nqoff;
+  // product as the B applies.  A pair of two floating substructures also
+  // keeps the rigid modes of the pair as a whole: they are continuous, so
+  // they lie in the range of Pi, and S annihilates them on both sides, so B
+  // does (and so does A: the averaging E leaves a continuous function as it
+  // is).  The eigenproblem lives on the complement of null(B) (the factor
+  // space); the iteration removes these directions from X and W.
+  DevBuf nQ, nT, nqoff, pQ, pqoff, pnull_d;
   int nr = 0;
-  bool nullproj = false;
+  bool nullproj = false, pairdefl = false;
+  std::vector<int> pnull(np, 0);   // rigid modes of the pair as a whole (both sides floating)
   if (lvl == 1) {
     const int dpn = mesh.dpn;
     nr = dpn == 1 ? 1 : 6;
@@ -1173,45 +1247,58 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       }
       if (dir) touched[mesh.elem_sub_h[e]] = 1;
     }
+    auto node_xyz = [&](int64_t dof, double* c3) {
+      const int64_t node = dof / dpn;
+      c3[0] = (double)(node % (nx + 1));
+      c3[1] = (double)((node / (nx + 1)) % (ny + 1));
+      c3[2] = (double)(node / ((int64_t)(nx + 1) * (ny + 1)));
+    };
+    // the interface centroid of substructure s (accumulated into cen with
+    // weight 1 / total)
+    auto add_centroid = [&](int s2, double total, double* cen) {
+      const SubTopo& sb = tp.subs[s2];
+      for (int l = 0; l < L.ng[s2]; ++l) {
+        double c3[3];
+        node_xyz(sb.dofs[sb.n_i + l], c3);
+        for (int a2 = 0; a2 < 3; ++a2) cen[a2] += c3[a2] / total;
+      }
+    };
+    // rigid modes on substructure s2's interface about cen: column k at
+    // out + k * ld, rows row0 .. row0 + n_g
+    auto fill_modes = [&](int s2, const double* cen, double* out, int64_t ld, int64_t row0) {
+      const SubTopo& sb = tp.subs[s2];
+      for (int l = 0; l < L.ng[s2]; ++l) {
+        double* q = out + row0 + l;
+        if (dpn == 1) {
+          q[0] = 1.0;
+          continue;
+        }
+        const int64_t dof = sb.dofs[sb.n_i + l];
+        const int comp = (int)(dof % dpn);
+        double c3[3];
+        node_xyz(dof, c3);
+        const double px = c3[0] - cen[0], py = c3[1] - cen[1], pz = c3[2] - cen[2];
+        q[(int64_t)comp * ld] = 1.0;   // translations
+        // rotations w x p about the three axes, component `comp`
+        const double rx[3] = {0.0, -pz, py}, ry[3] = {pz, 0.0, -px}, rz[3] = {-py, px, 0.0};
+        q[3 * ld] = rx[comp];
+        q[4 * ld] = ry[comp];
+        q[5 * ld] = rz[comp];
+      }
+    };
     std::vector<int64_t> qoff(L.ns, -1), foff;
     std::vector<int32_t> fng;
     std::vector<double> hq;
-    for (int s = 0; s < L.ns; ++s) {
-      if (touched[s] || L.ng[s] < nr) continue;
-      const SubTopo& sb = tp.subs[s];
-      const int n = L.ng[s];
-      qoff[s] = (int64_t)hq.size();
-      foff.push_back(qoff[s]);
+    for (int s2 = 0; s2 < L.ns; ++s2) {
+      if (touched[s2] || L.ng[s2] < nr) continue;
+      const int n = L.ng[s2];
+      qoff[s2] = (int64_t)hq.size();
+      foff.push_back(qoff[s2]);
       fng.push_back(n);
-      // node coordinates relative to the substructure's interface centroid
-      std::vector<double> xyz((size_t)3 * n);
       double cen[3] = {0.0, 0.0, 0.0};
-      for (int l = 0; l < n; ++l) {
-        const int64_t node = sb.dofs[sb.n_i + l] / dpn;
-        const double c3[3] = {(double)(node % (nx + 1)), (double)((node / (nx + 1)) % (ny + 1)),
-                              (double)(node / ((int64_t)(nx + 1) * (ny + 1)))};
-        for (int a = 0; a < 3; ++a) {
-          xyz[(size_t)3 * l + a] = c3[a];
-          cen[a] += c3[a] / n;
-        }
-      }
+      add_centroid(s2, n, cen);
       hq.resize(hq.size() + (size_t)n * nr, 0.0);
-      double* qs = hq.data() + qoff[s];
-      for (int l = 0; l < n; ++l) {
-        if (dpn == 1) {
-          qs[l] = 1.0;
-          continue;
-        }
-        const int comp = (int)(sb.dofs[sb.n_i + l] % dpn);
-        const double px = xyz[(size_t)3 * l] - cen[0], py = xyz[(size_t)3 * l + 1] - cen[1],
-                     pz = xyz[(size_t)3 * l + 2] - cen[2];
-        qs[(size_t)comp * n + l] = 1.0;   // translations
-        // rotations w x p about the three axes, component `comp`
-        const double rx[3] = {0.0, -pz, py}, ry[3] = {pz, 0.0, -px}, rz[3] = {-py, px, 0.0};
-        qs[(size_t)3 * n + l] = rx[comp];
-        qs[(size_t)4 * n + l] = ry[comp];
-        qs[(size_t)5 * n + l] = rz[comp];
-      }
+      fill_modes(s2, cen, hq.data() + qoff[s2], n, 0);
     }
     if (!foff.empty()) {
       nullproj = true;
@@ -1224,10 +1311,42 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       k_orth_modes<<<(unsigned)foff.size(), 256, 0, st>>>(dptr<double>(nQ), dptr<int64_t>(dfoff), dptr<int32_t>(dfng), nr);
       AMB_LAUNCHED();
       std::vector<GemmDesc> d;
-      for (int s = 0; s < L.ns; ++s)
-        if (qoff[s] >= 0) d.push_back(GemmDesc{L.ng[s], nr, L.ng[s], L.ng[s], L.ng[s], L.ng[s], L.pS.off[s], qoff[s], qoff[s]});
+      for (int s2 = 0; s2 < L.ns; ++s2)
+        if (qoff[s2] >= 0) d.push_back(GemmDesc{L.ng[s2], nr, L.ng[s2], L.ng[s2], L.ng[s2], L.ng[s2], L.pS.off[s2], qoff[s2], qoff[s2]});
       gemm_batched<double, T>(st, ring, d, 0, 1.0, 0.0, dptr<T>(L.S), dptr<double>(nQ), dptr<double>(nT));
       AMB_CUDA(cudaStreamSynchronize(st));   // keep the host tables alive until the kernels ran
+    }
+    // pairs of two floating substructures: the pair's rigid modes on
+    // [Gamma^s; Gamma^t] about the pair's interface centroid
+    std::vector<int64_t> poff(np, -1), pfoff;
+    std::vector<int32_t> pfn;
+    std::vector<double> hp;
+    for (int p = 0; p < np; ++p) {
+      const int64_t* q = &qp[(size_t)p * Q_NPAIRF];
+      const int s2 = (int)q[Q_S], t2 = (int)q[Q_T];
+      if (qoff[s2] < 0 || qoff[t2] < 0) continue;
+      const int64_t N = q[Q_N];
+      pnull[p] = nr;
+      poff[p] = (int64_t)hp.size();
+      pfoff.push_back(poff[p]);
+      pfn.push_back((int32_t)N);
+      double cen[3] = {0.0, 0.0, 0.0};
+      add_centroid(s2, (double)N, cen);
+      add_centroid(t2, (double)N, cen);
+      hp.resize(hp.size() + (size_t)N * nr, 0.0);
+      fill_modes(s2, cen, hp.data() + poff[p], N, 0);
+      fill_modes(t2, cen, hp.data() + poff[p], N, q[Q_NS]);
+    }
+    if (!pfoff.empty()) {
+      pairdefl = true;
+      DevBuf dpfoff, dpfn;
+      upload(pQ, hp, st);
+      upload(pqoff, poff, st);
+      upload(dpfoff, pfoff, st);
+      upload(dpfn, pfn, st);
+      k_orth_modes<<<(unsigned)pfoff.size(), 256, 0, st>>>(dptr<double>(pQ), dptr<int64_t>(dpfoff), dptr<int32_t>(dpfn), nr);
+      AMB_LAUNCHED();
+      AMB_CUDA(cudaStreamSynchronize(st));
     }
   }
   // pseudo-inverse of the pair coarse matrices (initial constraints)
@@ -1235,8 +1354,10 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     const int nl = max_ncp + (max_ncp & 1);
     const size_t smem = (size_t)2 * nl * nl * sizeof(double);
     AMB_CUDA(cudaFuncSetAttribute(k_pair_pinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1)));
+    upload(pnull_d, pnull, st);
     k_pair_pinv<T><<<np, kJacobiThreads, smem, st>>>(dptr<T>(Pinv), QPd, dptr<double>(L.Ac), dptr<int64_t>(dacs),
-                                          dptr<int64_t>(dact), dptr<int32_t>(dcms), dptr<int32_t>(dcmt), dptr<int>(status));
+                                          dptr<int64_t>(dact), dptr<int32_t>(dcms), dptr<int32_t>(dcmt),
+                                          dptr<int>(pnull_d), dptr<int>(status));
     AMB_LAUNCHED();
   }
 
@@ -1513,10 +1634,18 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   };
 
   // ------------------------------------------------ LOBPCG
+  // the factor space: the pair rigid modes out of a slot's leading columns
+  auto deflate = [&](int slot, const int* ncol) {
+    if (!pairdefl) return;
+    k_lob_deflate<<<np, 256, 0, st>>>(Q, QPd, slot, m, dptr<int>(act_d), dptr<int64_t>(pqoff), dptr<double>(pQ), nr,
+                                      ncol);
+    AMB_LAUNCHED();
+  };
   k_lob_random<V><<<dim3(nblk(maxN * 9 * m), np), 256, 0, st>>>(Q, QPd, m, cfg.opt.seed + 7919ull * lvl);
   AMB_LAUNCHED();
   AMB_CUDA(cudaMemcpyAsync(act_d.p, active.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
   project(Q, Q_OQ, 0, m);
+  deflate(0, nullptr);
   applyA(0, 3);
   applyB(0, 6);
   rayleigh_ritz(m);
@@ -1525,19 +1654,24 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
   const int maxit = std::max(1, cfg.opt.lobpcg_maxit);
   const double tau = cfg.tau;
   std::vector<double> resid(np, 0.0), best(np, 1e300), prev((size_t)np * m, -1e300);
-  std::vector<int> since(np, 0);
-  // stagnation: far from tol, kStall iterations without halving the worst
+  std::vector<int> since(np, 0), stable(np, 0);
+  // Convergence: every used column's residual at most tol, or every used
+  // Ritz value still to kRitzTol (relative) for kRitzStable iterations in a
+  // row.  The columns of very large eigenvalues (a stiff inclusion across
+  // the face, lambda ~ 1e5 tau) have a residual floor far above tol: their
+  // eigenvector's B-energy is tiny against its Euclidean norm, so the
+  // residual's components along B's large eigenvalues dominate it, while
+  // the Ritz value converges (quadratically in the eigenvector's error) to
+  // the pencil's.  Iterating on after that lets rounding in [X W P] bring
+  // spurious directions back into the basis.
+  // Stagnation: far from tol, kStall iterations without halving the worst
   // used residual; within kFloor x tol (the residual floor of the operator
   // products, reached by some pairs of the FP32 form), kFloorStall.
   // FP64 form: a used Ritz value that still rises by more than tol (relative)
-  // also counts as progress.  The columns of very large eigenvalues (a stiff
-  // inclusion across the face, lambda ~ 1e5 tau) have a residual floor far
-  // above tol, because B w is tiny against B's norm there, while their Ritz
-  // values still converge; without this rule such a pair stops with its top
-  // eigenvalue a few 1e-4 low.  Ritz values of the FP32 form carry the FP32
-  // pencil's noise, so that form keeps the residual rule alone.
-  constexpr int kStall = 20, kFloorStall = 3;
-  constexpr double kFloor = 10.0;
+  // also counts as progress.  Ritz values of the FP32 form carry the FP32
+  // pencil's noise, so that form keeps the residual rule alone there.
+  constexpr int kStall = 20, kFloorStall = 3, kRitzStable = 2;
+  constexpr double kFloor = 10.0, kRitzTol = 1e-10;
   constexpr bool kRitzProgress = sizeof(T) == sizeof(double);
   auto check = [&]() {
     k_lob_resid<V><<<dim3(np, m), 256, 0, st>>>(Q, dptr<double>(rn), dptr<double>(bn), dptr<double>(lam), QPd, m, dptr<int>(act_d));
@@ -1557,17 +1691,20 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       kuse = std::min(m, kuse + 1);
       nwh[p] = std::min(m, kuse + kGuard);
       double worst = 0.0;
-      bool rising = false;
+      bool rising = false, still = true;
       for (int k = 0; k < kuse; ++k) {
         const double l = hl[(size_t)p * m + k];
         const double b = hb[(size_t)p * m + k];
         if (kRitzProgress && l - prev[(size_t)p * m + k] > tol * std::max(std::fabs(l), lref)) rising = true;
+        if (!(std::fabs(l - prev[(size_t)p * m + k]) <= kRitzTol * std::max(std::fabs(l), lref))) still = false;
         if (b == 0.0) continue;   // dropped direction (rank-deficient pair space)
         const double ratio = hr[(size_t)p * m + k] / (std::max(std::fabs(l), lref) * b);
         worst = std::max(worst, std::isfinite(ratio) ? ratio : 1e300);
         if (!(ratio <= tol)) ok = false;
       }
       resid[p] = worst;
+      stable[p] = still ? stable[p] + 1 : 0;
+      ok = ok || stable[p] >= kRitzStable;
       conv[p] = ok ? 1 : 0;
       // a stagnating pair stops iterating (reported as not converged, with
       // its residual)
@@ -1598,6 +1735,7 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
                                                              dptr<int>(nw_d));
     AMB_LAUNCHED();
     applyM(1);
+    deflate(1, dptr<int>(nw_d));
     applyA(1, 4);
     applyB(1, 7);
     rayleigh_ritz(it == 0 ? 2 * m : 3 * m);

@@ -374,20 +374,21 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
 
 // ---------------------------------------------------------------- FP64 form: exact slice products
 //
-// C(lower) += alpha P P^T in FP64 accuracy on the TF32 tensor cores.  Row r of
-// P (one trailing-update panel, K <= 256) is scaled by 2^-e_r, e_r the
-// exponent of its largest entry, and cut into kOzSlices integer slices:
-// v = P(r, k) 2^-e_r in (-1, 1); t = 128 v, m_0 = rint(t), v = t - m_0; and
-// so on, so P(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-56 of the row's
-// largest entry, |m_0| <= 128, |m_p| <= 64.  These small integers are exact
-// in TF32 and so are their products; the products of slices p and q with
-// p + q = l go to TMEM accumulator l.  Per K-step a level collects at most
-// 2^14 + (l - 1) 2^12 (l >= 1) or 2^14 (l = 0), so over K = 256 every
-// partial sum is an integer below 10 * 2^20 < 2^24: exact in the FP32
-// accumulator whatever its rounding mode.  Products with p + q >= kOzSlices
-// are dropped (below 2^-49 of 2^(e_i + e_j)).  The epilogue adds the levels
-// times 2^-7(l+2) in FP32 pairs, smallest first (about 48 bits), and updates
-// C in FP64 with the factor 2^(e_i + e_j).
+// C = beta C + alpha A B^T in FP64 accuracy on the TF32 tensor cores (the
+// Cholesky trailing updates, C lower and B = A, and the triangular-inverse
+// merges).  Every row r of an operand chunk (K <= 256) is scaled by 2^-e_r,
+// e_r the exponent of its largest entry, and cut into kOzSlices integer
+// slices: v = X(r, k) 2^-e_r in (-1, 1); t = 128 v, m_0 = rint(t),
+// v = t - m_0; and so on, so X(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-56
+// of the row's largest entry, |m_0| <= 128, |m_p| <= 64.  These small
+// integers are exact in TF32 and so are their products; the products of
+// slices p and q with p + q = l go to TMEM accumulator l.  Per K step a
+// level collects at most 2^14 + (l - 1) 2^12 (l >= 1) or 2^14 (l = 0), so
+// over K = 256 every partial sum is an integer below 10 * 2^20 < 2^24: exact
+// in the FP32 accumulator whatever its rounding mode.  Products with
+// p + q >= kOzSlices are dropped (below 2^-49 of 2^(e_i + e_j) each).  The
+// epilogue forms sum_l L_l 2^(7 (7 - l)) as an exact integer and rounds
+// it times 2^(e_i + e_j - 63) to FP64 once; the C update is one FP64 FMA.
 //
 // Tiles are 128 x 64 (M x N): the eight accumulators of a tile fill the 512
 // TMEM columns.  Per K step of 32 the B rows of all slices (8 x 8 KB) sit in
@@ -439,45 +440,89 @@ __device__ __forceinline__ double oz_round(int64_t H, int64_t L, int s) {
   return __longlong_as_double((long long)bits);
 }
 
-// source rows x cols (column form: (r, k) at src + r + k * ld) -> slab rows
-// row0 .. row0 + rpad of every slice (slice p at slab row p * R + row), K
-// contiguous with stride kp; rows and columns outside the block are zero.
-// One thread per row: the reads along k are coalesced across the warp.
-__global__ void __launch_bounds__(128) k_oz_split(const TcSplitDesc* d, int kp, int64_t R, float* slab, int* ex) {
-  const TcSplitDesc x = d[blockIdx.y];
-  const int r = blockIdx.x * 128 + threadIdx.x;
-  if (r >= x.rpad) return;
+// FP64 source block (rows x cols; column form: (r, k) at src + r + k*ld,
+// K-major form: src + k + r*ld; triangle masks as in the FP32 split) -> the
+// slices of slab rows [row0, row0 + rpad) (slice p at slab row p * R + row),
+// K contiguous with stride kp, and the row exponents ex[row].  A CTA takes
+// 128 rows through shared memory in 32-column tiles (reads coalesced along
+// the source's contiguous direction) twice: once for the row maxima, once
+// to cut the slices; eight threads write one slab row's 128 bytes per slice.
+__device__ __forceinline__ void oz_load_tile(const TcSplitDesc& x, int r0, int k0, int tid, double (*t)[kSplitRows + 1]) {
   const double* src = reinterpret_cast<const double*>(x.src);
-  const bool in = r < x.rows;
-  double mx = 0.0;
-  if (in)
-    for (int k = 0; k < x.cols; ++k) mx = fmax(mx, fabs(src[r + (int64_t)k * x.ld]));
-  int e = 0;
-  if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |P(r, k)| 2^-e < 1
-  ex[x.row0 + r] = e;
-  for (int k0 = 0; k0 < kp; k0 += 4) {
-    float sl[kOzSlices][4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int k = k0 + u;
-      double v = (in && k < x.cols) ? ldexp(src[r + (int64_t)k * x.ld], -e) : 0.0;
-#pragma unroll
-      for (int p = 0; p < kOzSlices; ++p) {
-        const double t = v * 128.0;
-        const double m = rint(t);
-        v = t - m;
-        sl[p][u] = (float)m;
-      }
+  if (x.kmajor) {
+    const int k = k0 + (tid & 31);
+    for (int rr = tid >> 5; rr < kSplitRows; rr += 8) {
+      const int r = r0 + rr;
+      bool ok = r < x.rows && k < x.cols;
+      if (x.tri == 1 && k - r > x.diag) ok = false;
+      if (x.tri == 2 && k - r < x.diag) ok = false;
+      t[tid & 31][rr] = ok ? src[k + (int64_t)r * x.ld] : 0.0;
     }
-#pragma unroll
-    for (int p = 0; p < kOzSlices; ++p)
-      *reinterpret_cast<float4*>(slab + (p * R + x.row0 + r) * (int64_t)kp + k0) =
-          make_float4(sl[p][0], sl[p][1], sl[p][2], sl[p][3]);
+  } else {
+    for (int idx = tid; idx < 32 * kSplitRows; idx += 256) {
+      const int rr = idx % kSplitRows, kk = idx / kSplitRows;
+      const int r = r0 + rr, k = k0 + kk;
+      bool ok = r < x.rows && k < x.cols;
+      if (x.tri == 1 && k - r > x.diag) ok = false;
+      if (x.tri == 2 && k - r < x.diag) ok = false;
+      t[kk][rr] = ok ? src[r + (int64_t)k * x.ld] : 0.0;
+    }
   }
 }
 
-// tile t of a lower 128 x 64 tiling of an m x m matrix: row tile ti has
-// min(2 ti + 2, tn) column tiles
+__global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, int64_t R, float* slab, int* ex) {
+  __shared__ double t[32][kSplitRows + 1];   // [k][r]
+  __shared__ int esh[kSplitRows];
+  const TcSplitDesc x = d[blockIdx.y];
+  const int r0 = blockIdx.x * kSplitRows;
+  if (r0 >= x.rpad) return;
+  const int tid = threadIdx.x;
+  const int kc = (x.cols + kTK - 1) / kTK * kTK;   // the K range the tiles read
+  double mx = 0.0;
+  for (int k0 = 0; k0 < kc; k0 += 32) {
+    oz_load_tile(x, r0, k0, tid, t);
+    __syncthreads();
+    if (tid < kSplitRows)
+      for (int kk = 0; kk < 32; ++kk) mx = fmax(mx, fabs(t[kk][tid]));
+    __syncthreads();
+  }
+  if (tid < kSplitRows) {
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |X(r, k)| 2^-e < 1
+    esh[tid] = e;
+    ex[x.row0 + r0 + tid] = e;
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < kc; k0 += 32) {
+    oz_load_tile(x, r0, k0, tid, t);
+    __syncthreads();
+    // 128 rows x 8 groups of 4 k: thread -> (row, k group)
+    for (int idx = tid; idx < kSplitRows * 8; idx += 256) {
+      const int g = idx & 7, rr = idx >> 3;
+      const int e = esh[rr];
+      float sl[kOzSlices][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        double v = ldexp(t[4 * g + u][rr], -e);
+#pragma unroll
+        for (int p = 0; p < kOzSlices; ++p) {
+          const double tt = v * 128.0;
+          const double m = rint(tt);
+          v = tt - m;
+          sl[p][u] = (float)m;
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < kOzSlices; ++p)
+        *reinterpret_cast<float4*>(slab + (p * R + x.row0 + r0 + rr) * (int64_t)kp + k0 + 4 * g) =
+            make_float4(sl[p][0], sl[p][1], sl[p][2], sl[p][3]);
+    }
+    __syncthreads();
+  }
+}
+
+// tile t of a descriptor: lower (square C, 128 x 64 tiles, row tile ti has
+// min(2 ti + 2, tn) column tiles) or dense (row-major over tm x tn tiles)
 __device__ __forceinline__ void oz_tile(const TcTileArgs& g, int tile, TcDesc& d, int& ti, int& tj) {
   int lo = 0, hi = g.ndesc - 1;
   while (lo < hi) {
@@ -486,10 +531,16 @@ __device__ __forceinline__ void oz_tile(const TcTileArgs& g, int tile, TcDesc& d
   }
   d = g.desc[lo];
   const int t = tile - g.prefix[lo];
-  ti = (int)((sqrtf(4.f * t + 1.f) - 1.f) * 0.5f);
-  while (ti * (ti + 1) > t) --ti;
-  while ((ti + 1) * (ti + 2) <= t) ++ti;
-  tj = t - ti * (ti + 1);
+  if (d.lower) {
+    ti = (int)((sqrtf(4.f * t + 1.f) - 1.f) * 0.5f);
+    while (ti * (ti + 1) > t) --ti;
+    while ((ti + 1) * (ti + 2) <= t) ++ti;
+    tj = t - ti * (ti + 1);
+  } else {
+    const int tn = (d.n + kOzTN - 1) / kOzTN;
+    ti = t / tn;
+    tj = t % tn;
+  }
 }
 
 struct OzArgs {
@@ -503,7 +554,7 @@ struct OzArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUtensorMap map_a,
+__global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUtensorMap map_a,
                                                    const __grid_constant__ CUtensorMap map_b, OzArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bfull[kOzBBufs], bempty[kOzBBufs], afull[kOzAStages], aempty[kOzAStages], tfull,
@@ -556,9 +607,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUte
         int ti, tj;
         oz_tile(g, tile, d, ti, tj);
         const int64_t ya = d.arow + (int64_t)ti * kTM, yb = d.brow + (int64_t)tj * kOzTN;
-        const int nk = d.k / kTK;
+        int kb, ke;
+        tile_krange(d, ti, kb, ke);
         bool ok = true;
-        for (int kt = 0; kt < nk && ok; ++kt, ++ib) {
+        for (int kt = kb; kt < ke && ok; ++kt, ++ib) {
           const int sb = ib % kOzBBufs;
           if (!role_wait(smem_u32(&bempty[sb]), ((ib / kOzBBufs) & 1) ^ 1, &abort_sh, g.status)) break;
           const uint32_t bdst = smem_u32(bbuf + sb * kOzBBytes), bfb = smem_u32(&bfull[sb]);
@@ -585,11 +637,12 @@ __global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUte
         TcDesc d;
         int ti, tj;
         oz_tile(g, tile, d, ti, tj);
-        const int nk = d.k / kTK;
+        int kb, ke;
+        tile_krange(d, ti, kb, ke);
         if (!role_wait(smem_u32(&tempty), (tl & 1) ^ 1, &abort_sh, g.status)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         bool ok = true;
-        for (int kt = 0; kt < nk && ok; ++kt, ++ib) {
+        for (int kt = kb; kt < ke && ok; ++kt, ++ib) {
           const int sb = ib % kOzBBufs;
           if (!role_wait(smem_u32(&bfull[sb]), (ib / kOzBBufs) & 1, &abort_sh, g.status)) break;
           const uint32_t bsrc = smem_u32(bbuf + sb * kOzBBytes);
@@ -605,10 +658,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUte
             for (int kk = 0; kk < kTK / 8; ++kk) {
               const uint32_t ko = kk * 32;   // K = 8 per MMA: 32 bytes along the swizzled row
               const uint64_t da = smem_desc_sw128(asrc + ko);
-              // the first product into each level starts it: level l first sees (p, q) = (0, l)
+              // level l is started by its first product, (p, q) = (0, l)
               for (int q = 0; q < kOzSlices - p; ++q)
                 mma_tf32_n64(tacc + (uint32_t)((p + q) * kOzTN), da, smem_desc_sw128(bsrc + q * kOzBTile + ko),
-                             (kt > 0 || p > 0 || kk > 0) ? 1u : 0u);
+                             (kt > kb || p > 0 || kk > 0) ? 1u : 0u);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&aempty[sa]))
@@ -631,13 +684,21 @@ __global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUte
       TcDesc d;
       int ti, tj;
       oz_tile(g, tile, d, ti, tj);
+      int kb, ke;
+      tile_krange(d, ti, kb, ke);
+      const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
+      const int jlast = min(d.n, d.lower ? i + 1 : d.n) - 1 - tj * kOzTN;   // last tile column this row updates
+      const double beta = d.first ? ga.beta : 1.0;
+      double* const crow = ga.c + d.c + i + (int64_t)tj * kOzTN * d.ldc;
+      // C's lines into L2 while the tile's products run
+      if (i < d.m && beta != 0.0)
+        for (int q = 0; q <= min(jlast, kOzTN - 1); ++q)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(crow + (int64_t)q * d.ldc));
+      const int ei = ga.ex[d.arow + i];
       if (!role_wait(smem_u32(&tfull), tl & 1, &abort_sh, g.status)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int i = ti * kTM + quad * 32 + lane;   // row of C within the product
-      const bool row_ok = i < d.m;
-      const int ei = ga.ex[d.arow + min(i, d.m - 1)];
-      double* const crow = ga.c + d.c + i;
-#pragma unroll 1
+      double v[kOzTN];
+#pragma unroll
       for (int h = 0; h < kOzTN / 16; ++h) {
         // levels 0..3 -> H, levels 4..7 -> L: the product is (H 2^28 + L) 2^-63
         // in units of 2^(e_i + e_j), both parts exact in int64 (below 2^46)
@@ -659,28 +720,42 @@ __global__ void __launch_bounds__(192, 1) k_oz_syrk(const __grid_constant__ CUte
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
-            int64_t v = 0;
+            int64_t w = 0;
 #pragma unroll
-            for (int a = 0; a < 4; ++a) v = v * 128 + (int64_t)__float2int_rn(__uint_as_float(r[a][q]));
-            part[half][q] = v;
+            for (int a = 0; a < 4; ++a) w = w * 128 + (int64_t)__float2int_rn(__uint_as_float(r[a][q]));
+            part[half][q] = w;
           }
         }
-        if (row_ok) {
-          const int j0 = tj * kOzTN + h * 16;
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
-            const int j = j0 + q;
-            if (j < d.n && j <= i) {
-              const double v = oz_round(part[0][q], part[1][q], ei + ga.ex[d.brow + j] - 63);
-              double* cp = crow + (int64_t)j * d.ldc;
-              *cp = ga.beta == 1.0 ? fma(ga.alpha, v, *cp) : fma(ga.alpha, v, ga.beta * *cp);
-            }
-          }
+        for (int q = 0; q < 16; ++q) {
+          const int j = tj * kOzTN + h * 16 + q;
+          // a tile without K steps (a triangular operand with no entries in
+          // this chunk) has no accumulator data: its product is zero
+          v[h * 16 + q] = (kb < ke && j < d.n) ? oz_round(part[0][q], part[1][q], ei + ga.ex[d.brow + j] - 63) : 0.0;
         }
       }
+      // TMEM back to the MMA warp before the C traffic
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty)) : "memory");
+      if (i < d.m) {
+        // 16 columns at a time: the loads first, then the stores
+#pragma unroll
+        for (int cb = 0; cb < kOzTN / 16; ++cb) {
+          double cv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int jj = cb * 16 + q;
+            cv[q] = (jj <= jlast && beta != 0.0) ? __ldcg(crow + (int64_t)jj * d.ldc) : 0.0;
+          }
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int jj = cb * 16 + q;
+            if (jj <= jlast) crow[(int64_t)jj * d.ldc] = beta == 1.0 ? fma(ga.alpha, v[jj], cv[q])
+                                                                     : fma(ga.alpha, v[jj], beta * cv[q]);
+          }
+        }
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -817,35 +892,25 @@ void tc_syrk_lower(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d
   run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, base, status);
 }
 
-void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
-                       double* base, int* status) {
-  if (d.empty()) return;
+namespace {
+
+int oz_tile_count(const TcDesc& x) {
+  if (x.m <= 0 || x.n <= 0) return 0;
+  const int tm = (x.m + kTM - 1) / kTM, tn = (x.n + kOzTN - 1) / kOzTN;
+  if (x.lower) return tm * (tm + 1) - (2 * tm - tn);   // row tile ti holds min(2 ti + 2, tn) column tiles
+  return tm * tn;
+}
+
+// one split launch over sp, then one persistent tile launch over td (FP64 data)
+void run_oz(cudaStream_t st, DescRing& ring, const std::vector<TcSplitDesc>& sp, const std::vector<TcDesc>& td,
+            std::vector<int> prefix, int64_t rows, int maxr, int64_t tiles, double alpha, double beta, double* cbase,
+            int* status) {
   constexpr int kp = kTcKMax;
-  std::vector<TcSplitDesc> sp;
-  std::vector<TcDesc> td;
-  std::vector<int> prefix;
-  int64_t rows = 0, tiles = 0;
-  int maxr = 0;
-  for (const auto& x : d) {
-    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
-    if (x.rem <= 0 || x.k <= 0) continue;
-    const int rpad = pad_rows(x.rem);
-    // the split pass reads the FP64 source through the descriptor's pointer
-    sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(base + x.p), rows, x.ld, x.rem, x.k, rpad, 0, 0, 0, 0});
-    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0, 0, 1};
-    prefix.push_back((int)tiles);
-    const int tm = (x.rem + kTM - 1) / kTM, tn = (x.rem + kOzTN - 1) / kOzTN;
-    tiles += tm * (tm + 1) - (2 * tm - tn);   // row tile ti holds min(2 ti + 2, tn) column tiles
-    td.push_back(t);
-    rows += rpad;
-    maxr = std::max(maxr, rpad);
-  }
-  if (td.empty()) return;
   AMB_CHECK(tiles < (1LL << 31) && rows * kOzSlices < (1LL << 31) && sp.size() < 65536, AMB_EINVAL,
             "tensor-core batch too large");
   static thread_local bool attr = false;
   if (!attr) {
-    AMB_CUDA(cudaFuncSetAttribute(k_oz_syrk, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemBytes));
+    AMB_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemBytes));
     attr = true;
   }
   static thread_local DevBuf slab_buf, ex_buf;
@@ -859,7 +924,8 @@ void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk
   int* ex = dptr<int>(ex_buf);
   prefix.push_back((int)tiles);
   const TcSplitDesc* dsp = static_cast<const TcSplitDesc*>(ring.push(sp.data(), sp.size() * sizeof(TcSplitDesc), st));
-  k_oz_split<<<dim3((unsigned)(maxr / 128), (unsigned)sp.size()), 128, 0, st>>>(dsp, kp, rows, slab, ex);
+  static_assert(kTM % kSplitRows == 0, "slab row padding must cover whole split tiles");
+  k_oz_split<<<dim3((unsigned)(maxr / kSplitRows), (unsigned)sp.size()), 256, 0, st>>>(dsp, kp, rows, slab, ex);
   AMB_LAUNCHED();
   std::vector<char> blob(td.size() * sizeof(TcDesc) + prefix.size() * sizeof(int));
   memcpy(blob.data(), td.data(), td.size() * sizeof(TcDesc));
@@ -872,7 +938,7 @@ void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk
   ga.R = rows;
   ga.alpha = alpha;
   ga.beta = beta;
-  ga.c = base;
+  ga.c = cbase;
   ga.ex = ex;
   ga.status = status;
   static thread_local int nsm = 0;
@@ -883,12 +949,15 @@ void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk
   }
   const CUtensorMap ma = slab_map(slab, rows * kOzSlices, kp, kTM), mb = slab_map(slab, rows * kOzSlices, kp, kOzTN);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, nsm);
-  k_oz_syrk<<<grid, 192, kOzSmemBytes, st>>>(ma, mb, ga);
+  k_oz_gemm<<<grid, 192, kOzSmemBytes, st>>>(ma, mb, ga);
   AMB_LAUNCHED();
 }
 
-void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,
-             const float* abase, const float* bbase, float* cbase, int* status) {
+// C = beta C + alpha A B^T for every entry of d, K in chunks of kTcKMax: per
+// chunk the split descriptors (B rows, then the A row ranges that have
+// entries in the chunk) and the tile descriptors, handed to run(...)
+template <typename E, class Count, class Run>
+void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, Count count, Run run) {
   constexpr int kp = kTcKMax;
   int kmax = 0;
   for (const auto& x : d) {
@@ -930,27 +999,74 @@ void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, floa
       // B rows (all n) for this chunk
       const int npad = pad_rows(x.n);
       const int64_t brow = rows;
-      sp.push_back(TcSplitDesc{bbase + x.b + (x.b_kmajor ? (int64_t)k0 : (int64_t)k0 * x.ldb), brow, x.ldb, x.n, kc,
-                               npad, x.b_kmajor, 0, 0, 0});
+      sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(bbase + x.b + (x.b_kmajor ? (int64_t)k0 : (int64_t)k0 * x.ldb)),
+                               brow, x.ldb, x.n, kc, npad, x.b_kmajor, 0, 0, 0});
       rows += npad;
       maxr = std::max(maxr, npad);
       for (int q = 0; q < nr; ++q) {
         const int r0 = rr[q][0], r1 = rr[q][1];
         const int mpad = pad_rows(r1 - r0);
         const int64_t aoff = x.a_kmajor ? (int64_t)k0 + (int64_t)r0 * x.lda : (int64_t)r0 + (int64_t)k0 * x.lda;
-        sp.push_back(TcSplitDesc{abase + x.a + aoff, rows, x.lda, r1 - r0, kc, mpad, x.a_kmajor, x.a_tri, r0 - k0, 0});
+        sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(abase + x.a + aoff), rows, x.lda, r1 - r0, kc, mpad,
+                                 x.a_kmajor, x.a_tri, r0 - k0, 0});
         TcDesc t{x.c + r0, rows, brow, r1 - r0, x.n, (kc + kTK - 1) / kTK * kTK, x.ldc, 0, x.a_tri, r0 - k0, rr[q][2]};
         prefix.push_back((int)tiles);
-        tiles += tc_tile_count(t);
+        tiles += count(t);
         td.push_back(t);
         rows += mpad;
         maxr = std::max(maxr, mpad);
       }
     }
     if (td.empty()) break;
-    run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, cbase, status);
+    run(sp, td, prefix, rows, maxr, tiles);
     if (kmax == 0) break;
   }
+}
+
+}  // namespace
+
+void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
+                       double* base, int* status) {
+  if (d.empty()) return;
+  constexpr int kp = kTcKMax;
+  std::vector<TcSplitDesc> sp;
+  std::vector<TcDesc> td;
+  std::vector<int> prefix;
+  int64_t rows = 0, tiles = 0;
+  int maxr = 0;
+  for (const auto& x : d) {
+    AMB_CHECK(x.k >= 0 && x.k <= kp, AMB_EINVAL, "tensor-core trailing update with K above the slab width");
+    if (x.rem <= 0 || x.k <= 0) continue;
+    const int rpad = pad_rows(x.rem);
+    // the split pass reads the FP64 source through the descriptor's pointer
+    sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(base + x.p), rows, x.ld, x.rem, x.k, rpad, 0, 0, 0, 0});
+    TcDesc t{x.c, rows, rows, x.rem, x.rem, (x.k + kTK - 1) / kTK * kTK, x.ld, 1, 0, 0, 1};
+    prefix.push_back((int)tiles);
+    tiles += oz_tile_count(t);
+    td.push_back(t);
+    rows += rpad;
+    maxr = std::max(maxr, rpad);
+  }
+  if (td.empty()) return;
+  run_oz(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, base, status);
+}
+
+void tc_gemm_f64(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, double alpha, double beta,
+                 const double* abase, const double* bbase, double* cbase, int* status) {
+  gemm_chunks(d, abase, bbase, oz_tile_count,
+              [&](const std::vector<TcSplitDesc>& sp, const std::vector<TcDesc>& td, const std::vector<int>& prefix,
+                  int64_t rows, int maxr, int64_t tiles) {
+                run_oz(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, cbase, status);
+              });
+}
+
+void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,
+             const float* abase, const float* bbase, float* cbase, int* status) {
+  gemm_chunks(d, abase, bbase, tc_tile_count,
+              [&](const std::vector<TcSplitDesc>& sp, const std::vector<TcDesc>& td, const std::vector<int>& prefix,
+                  int64_t rows, int maxr, int64_t tiles) {
+                run_tiles(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, cbase, status);
+              });
 }
 
 }  // namespace amb

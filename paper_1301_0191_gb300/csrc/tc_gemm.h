@@ -28,7 +28,8 @@ struct TcGemm {
 };
 
 // split pass: a rows x cols source block -> slab rows [row0, row0 + rpad),
-// entries outside it (and outside the triangle) zero
+// entries outside it (and outside the triangle) zero; src points to FP32 data
+// (FP32 form) or FP64 data (FP64 form)
 struct TcSplitDesc {
   const float* src;
   int64_t row0;
@@ -76,5 +77,11 @@ void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, floa
 constexpr int kOzSlices = 8;
 void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
                        double* base, int* status);
+
+// FP64 form: C = beta C + alpha A B^T for every entry of d, as tc_gemm, with
+// the exact slice products of tc_syrk_lower_f64 per K chunk of kTcKMax
+// (each chunk rounded to FP64 once and added to C in FP64).
+void tc_gemm_f64(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, double alpha, double beta,
+                 const double* abase, const double* bbase, double* cbase, int* status);
 
 }  // namespace amb

@@ -54,3 +54,23 @@ def test_fp64_schur_through_several_trailing_updates(B, sub, dpn, split, seed):
         print(f"sub {s}: n_I {ni} n_G {ng} max |S - S_oracle| / max |S| = {err:.3e}")
         assert err <= 1e-11, (s, err)
     ctx.close()
+
+
+@pytest.mark.parametrize("sub,dpn", [(12, 1), (9, 3)])
+def test_fp64_interior_inverse_through_the_tensor_core_merges(B, sub, dpn):
+    """One substructure, no interface: the preconditioner is the interior
+    solve Z^T Z with Z = L_I^-1 merged block by block on the tensor cores
+    (K up to 1024, several chunks per merge), so one PCG step leaves the
+    residual (I - K Z^T Z) f.  For Z to FP64 accuracy that is about
+    kappa(K) u ~ 10^3 x 1e-16; the test asks for 1e-11 (a Z of FP32 accuracy
+    leaves ~1e-4)."""
+    prob = ai.toy(sub, dpn, 44 + dpn, split=(1, 1, 1), sigma=1.5)
+    lev = olv.level_one(prob)
+    assert lev.subs[0].n_i > 2000 and lev.subs[0].n_g == 0
+    ctx = B.Context.from_problem(prob, adaptive=0)
+    f = ctx.load_vector(prob.body)
+    u, info = ctx.solve(f)
+    print(f"n_I {lev.subs[0].n_i}: iterations {info.iterations}, relative residual {info.rel_residual:.3e}")
+    assert info.iterations == 1
+    assert info.rel_residual <= 1e-11
+    ctx.close()

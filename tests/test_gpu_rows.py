@@ -68,12 +68,10 @@ def test_pair_rows_match_oracle(B, split, sub, dpn, seed, tau):
         rows = raw[: 8 * k * nf].view(np.float64).reshape(k, nf)
         dofs = raw[8 * k * nf:].view(np.int64)
         assert np.array_equal(dofs, free[res.face_dofs]), (p["s"], p["t"])
-        # a pair that stalls short of 1e-8 (the FP64 form keeps the floating
-        # substructures' rigid modes in the B operator, so the pencil is
-        # nearly singular there) stops at a residual set by rounding, which
-        # moves by tens of percent with the order of the Schur complement's
-        # arithmetic; the rows themselves are checked by principal angles
-        assert p["residual"] <= 1e-5, (p["s"], p["t"], p["residual"])
+        # a pair converges by its residual or by Ritz values that stay put to
+        # 1e-10 (relative); one that stalls short of 1e-8 stops at a residual
+        # set by rounding; the rows themselves are checked by principal angles
+        assert p["converged"] == 1 or p["residual"] <= 1e-5, (p["s"], p["t"], p["residual"])
         if _ambiguous(res.lam, tau, cap):
             continue
         assert p["n_selected"] == res.n_selected

@@ -149,6 +149,13 @@ def test_irregular_three_level_workload_sampled(B):
         res[name] = (ctx, info, rep)
         if name != "fp64":
             continue
+        # LOBPCG on the FP64 form: the stiff-slab faces (lambda_1 ~ 3e5)
+        # converge by their Ritz values; a pair that ends with a residual
+        # above 1e-2 has not found its eigenvectors (measured: 12 of 1344)
+        lost = [(p["s"], p["t"]) for p in rep["pairs"] if p["level"] == 1 and p["residual"] > 1e-2]
+        print(f"fp64 level-1 pairs with residual > 1e-2: {len(lost)} of 1344")
+        if len(lost) > 27:
+            bad.append(("lobpcg", len(lost), lost[:10]))
         # sampled against the oracle on crops: the face with the most rows, the
         # face with the largest pair eigenvalue, the face that sets the
         # indicator (its lambda_{k+1} is the level's omega, just below tau),
