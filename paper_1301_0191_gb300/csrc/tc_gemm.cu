@@ -161,12 +161,16 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// bounded wait that also gives up when another role has aborted
+// bounded wait that also gives up when another role has aborted.  try_wait
+// itself suspends the thread for a while before it reports false, so the
+// loop polls without sleeping for its first 4096 rounds (a sleep can
+// overshoot by microseconds, which the single MMA-issuing thread cannot
+// afford between pipeline stages) and backs off only after that.
 __device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* status) {
   for (long it = 0; it < kSpinLimit; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (it > 32) __nanosleep(64);
+    if (it > 4096) __nanosleep(64);
   }
   *abort_flag = 1;
   if (status) atomicCAS(status, 0, AMB_ETIMEOUT);
@@ -377,10 +381,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
 // C = beta C + alpha A B^T in FP64 accuracy on the TF32 tensor cores (the
 // Cholesky trailing updates, C lower and B = A, and the triangular-inverse
 // merges).  Every row r of an operand chunk (K <= 256) is scaled by 2^-e_r,
-// e_r the exponent of its largest entry, and cut into kOzSlices integer
-// slices: v = X(r, k) 2^-e_r in (-1, 1); t = 128 v, m_0 = rint(t),
-// v = t - m_0; and so on, so X(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-56
-// of the row's largest entry, |m_0| <= 128, |m_p| <= 64.  These small
+// e_r the exponent of its largest entry (|X(r, k)| < 2^e_r), rounded to the
+// 56-bit integer F = X(r, k) 2^(56 - e_r) and written in balanced base-128
+// digits: X(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-57 of 2^e_r, with
+// |m_0| <= 128 and |m_p| <= 64 for p >= 1 (integer arithmetic only).  These small
 // integers are exact in TF32 and so are their products; the products of
 // slices p and q with p + q = l go to TMEM accumulator l.  Per K step a
 // level collects at most 2^14 + (l - 1) 2^12 (l >= 1) or 2^14 (l = 0), so
@@ -400,34 +404,50 @@ constexpr int kOzATile = kTM * kTK * 4;                     // 16 KB
 constexpr int kOzBTile = kOzTN * kTK * 4;                   // 8 KB
 constexpr int kOzBBytes = kOzSlices * kOzBTile;             // 64 KB
 constexpr int kOzSmemBytes = kOzBBufs * kOzBBytes + kOzAStages * kOzATile + 1024;
-constexpr uint32_t kOzIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kOzTN >> 3) << 17) |
-                              ((uint32_t)(kTM >> 4) << 24);
 static_assert(kOzSlices * kOzTN <= 512, "the level accumulators must fit TMEM");
 static_assert(kOzSmemBytes <= 227 * 1024, "shared memory");
 
-__device__ __forceinline__ void mma_tf32_n64(uint32_t tacc, uint64_t a, uint64_t b, uint32_t accumulate) {
+// kind::tf32 instruction descriptor for M = 128 and N columns
+__host__ __device__ constexpr uint32_t oz_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32_idesc(uint32_t tacc, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
-      "l"(a), "l"(b), "r"(kOzIdesc), "r"(accumulate)
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
 }
 
-// (H 2^28 + L) 2^s rounded to the nearest double (ties to even), from the exact
-// 128-bit integer: one rounding however the two parts cancel
+// (H 2^28 + L) 2^s rounded to the nearest double (ties to even), |H|, |L| <
+// 2^46, in 64-bit integer arithmetic: the exact value is written as
+// +-(a 2^28 + b) with a >= 0, 0 <= b < 2^28; its top 53 bits are rounded
+// once, however H and L cancel
 __device__ __forceinline__ double oz_round(int64_t H, int64_t L, int s) {
-  const __int128 t = ((__int128)H << 28) + (__int128)L;
-  if (t == 0) return 0.0;
-  const bool neg = t < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  const uint64_t uh = (uint64_t)(u >> 64), ul = (uint64_t)u;
-  int nb = uh ? 128 - __clzll((long long)uh) : 64 - __clzll((long long)ul);   // bit length
-  uint64_t m;
-  if (nb <= 53) {
-    m = ul << (53 - nb);
+  int64_t hi = H + (L >> 28);   // floor division: L = (L >> 28) 2^28 + lo
+  uint64_t lo = (uint64_t)(L & ((1ll << 28) - 1));
+  const bool neg = hi < 0;
+  uint64_t a;
+  if (neg) {
+    // -(hi 2^28 + lo) = (-hi - 1) 2^28 + (2^28 - lo), or -hi 2^28 when lo == 0
+    a = lo ? (uint64_t)(-hi - 1) : (uint64_t)(-hi);
+    lo = lo ? (1ull << 28) - lo : 0ull;
   } else {
-    const int sh = nb - 53;
-    m = (uint64_t)(u >> sh);
-    const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1), half = (unsigned __int128)1 << (sh - 1);
+    a = (uint64_t)hi;
+  }
+  if (a == 0 && lo == 0) return 0.0;
+  uint64_t m;
+  int nb;   // bit length of a 2^28 + lo
+  if (a < (1ull << 25)) {
+    m = (a << 28) | lo;   // exact: below 2^53
+    nb = 64 - __clzll((long long)m);
+    m <<= 53 - nb;
+  } else {
+    const int la = 64 - __clzll((long long)a);
+    const int sh = la - 25;   // 1 .. 22: the bits of lo below the 53 kept ones
+    nb = la + 28;
+    m = (a << (28 - sh)) | (lo >> sh);
+    const uint64_t rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
     if (rem > half || (rem == half && (m & 1))) ++m;
     if (m >> 53) {
       m >>= 1;
@@ -470,6 +490,45 @@ __device__ __forceinline__ void oz_load_tile(const TcSplitDesc& x, int r0, int k
   }
 }
 
+// |x| as an ordered integer (the IEEE bit pattern without the sign)
+__device__ __forceinline__ uint64_t oz_absbits(double x) {
+  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// e with 2^(e-1) <= |x| < 2^e from the bits of |x| (x != 0)
+__device__ __forceinline__ int oz_exponent(uint64_t ab) {
+  const int bex = (int)(ab >> 52);
+  const uint64_t mant = (ab & 0xFFFFFFFFFFFFFull) | (bex ? (1ull << 52) : 0ull);
+  return (64 - __clzll((long long)mant)) + max(bex, 1) - 1075;
+}
+
+// the kOzSlices balanced base-128 digits of x 2^-e (|x| < 2^e): F = x 2^(56-e)
+// rounded to an integer (|F| < 2^56), least significant digit first, each
+// digit taken into (-64, 64] with a carry into the next
+__device__ __forceinline__ void oz_digits(double x, int e, float* dig) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const uint64_t ab = bits & 0x7FFFFFFFFFFFFFFFull;
+  const int bex = (int)(ab >> 52);
+  const uint64_t mant = (ab & 0xFFFFFFFFFFFFFull) | (bex ? (1ull << 52) : 0ull);
+  const int sh = max(bex, 1) - 1075 + 56 - e;   // <= 3
+  int64_t F;
+  if (sh >= 0) F = (int64_t)(mant << sh);
+  else if (sh > -64) F = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));
+  else F = 0;
+  const float sg = (bits >> 63) ? -1.f : 1.f;
+#pragma unroll
+  for (int p = kOzSlices - 1; p > 0; --p) {
+    int dd = (int)(F & 127);
+    F >>= 7;
+    if (dd > 64) {
+      dd -= 128;
+      F += 1;
+    }
+    dig[p] = sg * (float)dd;
+  }
+  dig[0] = sg * (float)F;   // 0 .. 128
+}
+
 __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, int64_t R, float* slab, int* ex) {
   __shared__ double t[32][kSplitRows + 1];   // [k][r]
   __shared__ int esh[kSplitRows];
@@ -478,17 +537,16 @@ __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, 
   if (r0 >= x.rpad) return;
   const int tid = threadIdx.x;
   const int kc = (x.cols + kTK - 1) / kTK * kTK;   // the K range the tiles read
-  double mx = 0.0;
+  uint64_t mx = 0;
   for (int k0 = 0; k0 < kc; k0 += 32) {
     oz_load_tile(x, r0, k0, tid, t);
     __syncthreads();
     if (tid < kSplitRows)
-      for (int kk = 0; kk < 32; ++kk) mx = fmax(mx, fabs(t[kk][tid]));
+      for (int kk = 0; kk < 32; ++kk) mx = max(mx, oz_absbits(t[kk][tid]));
     __syncthreads();
   }
   if (tid < kSplitRows) {
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |X(r, k)| 2^-e < 1
+    const int e = mx ? oz_exponent(mx) : 0;
     esh[tid] = e;
     ex[x.row0 + r0 + tid] = e;
   }
@@ -500,22 +558,13 @@ __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, 
     for (int idx = tid; idx < kSplitRows * 8; idx += 256) {
       const int g = idx & 7, rr = idx >> 3;
       const int e = esh[rr];
-      float sl[kOzSlices][4];
+      float sl[4][kOzSlices];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        double v = ldexp(t[4 * g + u][rr], -e);
-#pragma unroll
-        for (int p = 0; p < kOzSlices; ++p) {
-          const double tt = v * 128.0;
-          const double m = rint(tt);
-          v = tt - m;
-          sl[p][u] = (float)m;
-        }
-      }
+      for (int u = 0; u < 4; ++u) oz_digits(t[4 * g + u][rr], e, sl[u]);
 #pragma unroll
       for (int p = 0; p < kOzSlices; ++p)
         *reinterpret_cast<float4*>(slab + (p * R + x.row0 + r0 + rr) * (int64_t)kp + k0 + 4 * g) =
-            make_float4(sl[p][0], sl[p][1], sl[p][2], sl[p][3]);
+            make_float4(sl[0][p], sl[1][p], sl[2][p], sl[3][p]);
     }
     __syncthreads();
   }
@@ -645,28 +694,41 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
         for (int kt = kb; kt < ke && ok; ++kt, ++ib) {
           const int sb = ib % kOzBBufs;
           if (!role_wait(smem_u32(&bfull[sb]), (ib / kOzBBufs) & 1, &abort_sh, g.status)) break;
-          const uint32_t bsrc = smem_u32(bbuf + sb * kOzBBytes);
-          for (int p = 0; p < kOzSlices; ++p, ++ia) {
-            const int sa = ia % kOzAStages;
-            if (!role_wait(smem_u32(&afull[sa]), (ia / kOzAStages) & 1, &abort_sh, g.status)) {
+          // descriptors advance by (byte offset >> 4) in their address field:
+          // a slice tile is kOzBTile bytes, a K step of 8 is 32 bytes
+          const uint64_t db0 = smem_desc_sw128(smem_u32(bbuf + sb * kOzBBytes));
+          const uint32_t first = kt > kb ? 1u : 0u;
+#pragma unroll
+          for (int p = 0; p < kOzSlices; ++p) {
+            const int sa = (int)((ia + p) % kOzAStages);
+            if (!role_wait(smem_u32(&afull[sa]), ((ia + p) / kOzAStages) & 1, &abort_sh, g.status)) {
               ok = false;
               break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t asrc = smem_u32(abuf + sa * kOzATile);
+            const uint64_t da0 = smem_desc_sw128(smem_u32(abuf + sa * kOzATile));
+            // The B slices sit one after another in shared memory with the
+            // same 8-row group stride, and level p + q of slice q's product
+            // is TMEM column block p + q: so slices q = 0..3 (and 4..7-p)
+            // go in one MMA of N = 64 x (their count), written to the
+            // consecutive level blocks from p (and p + 4) on.  Level l is
+            // started by the first product into it, p = 0 and kk = 0 of the
+            // tile's first K step.
+            const int nq = kOzSlices - p, n1 = nq < 4 ? nq : 4, n2 = nq - n1;
 #pragma unroll
             for (int kk = 0; kk < kTK / 8; ++kk) {
-              const uint32_t ko = kk * 32;   // K = 8 per MMA: 32 bytes along the swizzled row
-              const uint64_t da = smem_desc_sw128(asrc + ko);
-              // level l is started by its first product, (p, q) = (0, l)
-              for (int q = 0; q < kOzSlices - p; ++q)
-                mma_tf32_n64(tacc + (uint32_t)((p + q) * kOzTN), da, smem_desc_sw128(bsrc + q * kOzBTile + ko),
-                             (kt > kb || p > 0 || kk > 0) ? 1u : 0u);
+              const uint32_t acc = (p > 0 || kk > 0) ? 1u : first;
+              mma_tf32_idesc(tacc + (uint32_t)(p * kOzTN), da0 + (uint64_t)(kk * 2), db0 + (uint64_t)(kk * 2),
+                             oz_idesc(n1 * kOzTN), acc);
+              if (n2 > 0)
+                mma_tf32_idesc(tacc + (uint32_t)((p + 4) * kOzTN), da0 + (uint64_t)(kk * 2),
+                               db0 + (uint64_t)(4 * (kOzBTile >> 4) + kk * 2), oz_idesc(n2 * kOzTN), acc);
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                              smem_u32(&aempty[sa]))
                          : "memory");
           }
+          ia += kOzSlices;
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&bempty[sb]))
                        : "memory");
@@ -726,12 +788,18 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
             part[half][q] = w;
           }
         }
+        int ej[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int j = tj * kOzTN + h * 16 + q;
+          ej[q] = j < d.n ? __ldg(ga.ex + d.brow + j) : 0;
+        }
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
           const int j = tj * kOzTN + h * 16 + q;
           // a tile without K steps (a triangular operand with no entries in
           // this chunk) has no accumulator data: its product is zero
-          v[h * 16 + q] = (kb < ke && j < d.n) ? oz_round(part[0][q], part[1][q], ei + ga.ex[d.brow + j] - 63) : 0.0;
+          v[h * 16 + q] = (kb < ke && j < d.n) ? oz_round(part[0][q], part[1][q], ei + ej[q] - 63) : 0.0;
         }
       }
       // TMEM back to the MMA warp before the C traffic
