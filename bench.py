@@ -412,17 +412,35 @@ def main():
     if not args.no_fp64_form and prec == B.FP32:
         # one untimed FP64 step first: it pays the one-time tile tuning of the FP64 products, as the
         # warm-up steps do for the FP32 form
+        # (the untimed step records the kernel families with CUDA events)
+        fam64 = None
         for timed in (False, True):
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
-            c64 = B.Context.from_problem(prob, coeff=coeff_d, precision=B.FP64, lobpcg_maxit=200, lobpcg_tol=1e-6)
+            c64 = B.Context.from_problem(prob, coeff=coeff_d, precision=B.FP64, lobpcg_maxit=200, lobpcg_tol=1e-6,
+                                         timing_events=0 if timed else 1)
             _, i64 = c64.solve(f_d, out=u_d)
             b.record()
             torch.cuda.synchronize()
+            if not timed:
+                fam64 = c64.stats()["families"]
             c64.close()
         fp64_form = {"s": a.elapsed_time(b) * 1e-3, "iterations": i64.iterations,
                      "speedup_fp32": a.elapsed_time(b) / ms, "warmup": 1}
+        tr = fam64["tc_trailing"]
+        if tr["ms"] > 0:
+            # the trailing updates C -= P P^T from exact slice products (k_oz_split + k_oz_gemm): FP64-accurate
+            # flops (2 per lower-triangle multiply-add) per second, against the nominal FP64 rate; each
+            # multiply-add is 36 TF32 slice products, against the TF32 tensor peak
+            rate = tr["flops"] / (tr["ms"] * 1e-3) / 1e12
+            fp64_form["trailing_update"] = {
+                "kernel": "k_oz_gemm (+ k_oz_split): C -= P P^T from eight 7-bit digit slices per entry on tcgen05",
+                "ms": tr["ms"], "launches": tr["launches"], "fp64_tflops": rate,
+                "vs_nominal_fp64_peak": rate / 1.25, "slice_product_tflops": 36 * rate,
+                "tensor_frac": 36 * rate / tf32_peak,
+                "note": "family time of the untimed FP64 step (CUDA events); the timed step runs without events"}
+        fp64_form["families_ms"] = {k: round(v["ms"], 1) for k, v in fam64.items() if v["ms"] > 0}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
