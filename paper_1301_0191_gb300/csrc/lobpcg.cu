@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "engine_impl.h"
+#include "tc_gemm.h"
 
 namespace amb {
 
@@ -1516,11 +1517,27 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
       const unsigned gx = (unsigned)std::min<int64_t>(nblk((int64_t)imax(L.nd) * m), 64);
       k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Xs), dptr<T>(Oin), dmap, m, 1);
       AMB_LAUNCHED();
-      gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Xs), dptr<T>(Zb));
-      gemm_batched<T>(st, ring, d2, G_TRANS_A | G_TUNE, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
-      gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
-      gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
-      gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb), dptr<T>(Xs));
+      if constexpr (std::is_same<T, double>::value) {
+        // FP64 form: the two triangular products with L_D^-1 (the bulk of the
+        // Neumann solve) from exact slice products on the tensor cores:
+        // C = A B^T with B(j, k) = Xs(k, j) (K-major), A = L_D^-1 (lower) or
+        // its transpose (K-major reads, upper)
+        std::vector<TcGemm> t1, t5;
+        for (const auto& g : d1) t1.push_back(TcGemm{g.a, g.b, g.c, g.lda, g.ldb, g.ldc, g.m, g.n, g.k, 0, 1, 1});
+        for (const auto& g : d5) t5.push_back(TcGemm{g.a, g.b, g.c, g.lda, g.ldb, g.ldc, g.m, g.n, g.k, 1, 1, 2});
+        tc_gemm_f64(st, ring, t1, 1.0, 0.0, dptr<double>(L.LinvD), dptr<double>(Xs), dptr<double>(Zb), dptr<int>(status));
+        gemm_batched<T>(st, ring, d2, G_TRANS_A | G_TUNE, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
+        gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
+        gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
+        tc_gemm_f64(st, ring, t5, 1.0, 0.0, dptr<double>(L.LinvD), dptr<double>(Zb), dptr<double>(Xs), dptr<int>(status));
+      } else {
+        gemm_batched<T>(st, ring, d1, G_TRI_A_LOWER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Xs), dptr<T>(Zb));
+        gemm_batched<T>(st, ring, d2, G_TRANS_A | G_TUNE, one, zero, dptr<T>(L.Y), dptr<T>(Zb), dptr<T>(Qc));
+        gemm_batched<T>(st, ring, d3, 0, one, zero, dptr<T>(L.Ginv), dptr<T>(Qc), dptr<T>(Qc));
+        gemm_batched<T>(st, ring, d4, 0, T(-1), one, dptr<T>(L.Y), dptr<T>(Qc), dptr<T>(Zb));
+        gemm_batched<T>(st, ring, d5, G_TRANS_A | G_TRI_A_UPPER | G_TUNE, one, zero, dptr<T>(L.LinvD), dptr<T>(Zb),
+                        dptr<T>(Xs));
+      }
       k_lob_neu_move<T><<<dim3(gx, (unsigned)nmap.size()), 256, 0, st>>>(dptr<T>(Oout), dptr<T>(Xs), dmap, m, 0);
       AMB_LAUNCHED();
     }
