@@ -77,6 +77,38 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+# cuBLAS GEMM rates measured on this machine's GB300 with `bench.py --measure-peaks` (8192^3, best of
+# three, torch matmul): TF32 tensor cores 1052 TFLOP/s, FP64 1.10 TFLOP/s, FP32 without tensor cores
+# 69.7 TFLOP/s, BF16 2015 TFLOP/s (MEASURED_PEAKS.json's BF16 burst: 1913).  The TF32 peak below is
+# the driver's measured BF16 burst times the measured TF32/BF16 ratio (0.522; nominal 1.1/2.25 = 0.489).
+MEASURED_TF32_PER_BF16 = 1051.8 / 2015.5
+MEASURED_FP64_TFLOPS = 1.10
+
+
+def measure_peaks():
+    """cuBLAS GEMM throughput (through torch) for the roofline denominators."""
+    def rate(dtype, n, reps, tf32=True):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(3):
+            a @ b
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            a @ b
+        e1.record()
+        torch.cuda.synchronize()
+        return 2 * n ** 3 / (e0.elapsed_time(e1) / reps * 1e-3) / 1e12
+    out = {"tf32_tflops": max(rate(torch.float32, 8192, 20) for _ in range(3)),
+           "fp32_no_tensor_tflops": max(rate(torch.float32, 8192, 5, False) for _ in range(2)),
+           "fp64_tflops": max(rate(torch.float64, 8192, 3) for _ in range(2)),
+           "bf16_tflops": max(rate(torch.bfloat16, 8192, 20) for _ in range(3)),
+           "method": "cuBLAS GEMM through torch, 8192^3, best of several"}
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------- clocks
 class Clocks:
     def __init__(self):
@@ -185,7 +217,12 @@ def main():
     ap.add_argument("--block", default="2,1,1", help="substructures per axis of the c2block workload")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, family timing, Schur sweep or baselines)")
+    ap.add_argument("--measure-peaks", action="store_true",
+                    help="print the cuBLAS GEMM rates (TF32, FP32, FP64, BF16) used as roofline peaks, then exit")
     args = ap.parse_args()
+    if args.measure_peaks:
+        measure_peaks()
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -300,10 +337,10 @@ def main():
     peaks, src = _peaks()
     fams = st["families"]
     fp = "fp32" if prec == B.FP32 else "fp64"
-    # SIMT FP32: 152 SMs x 128 lanes x 2 flops x max SM clock; FP64: nominal 1.25 TFLOP/s
-    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if fp == "fp32" else 1.25
-    # TF32 tensor peak: the measured dense BF16 burst times the nominal TF32/BF16 ratio (1.1 / 2.25 PFLOP/s)
-    tf32_peak = peaks["bf16_tflops"] * (1.1 / 2.25)
+    # SIMT FP32: 152 SMs x 128 lanes x 2 flops x max SM clock; FP64: the measured cuBLAS FP64 GEMM rate
+    alu_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12 if fp == "fp32" else MEASURED_FP64_TFLOPS
+    # TF32 tensor peak: the measured dense BF16 burst times the measured cuBLAS TF32/BF16 ratio
+    tf32_peak = peaks["bf16_tflops"] * MEASURED_TF32_PER_BF16
     # per-substructure sizes of level 1: (n_I, n_Gamma, n_corner, n_c)
     sz = np.array([c.export(B.X_SUB_SIZES, 1, s, np.int32)[:4] for s in range(li.n_subs)], dtype=np.float64)
     n_i, n_g, n_d = sz[:, 0], sz[:, 1], sz[:, 1] - sz[:, 2]
@@ -332,7 +369,7 @@ def main():
             peak, peak_src = pair_peak, (f"derived FP32-pair multiply-add rate: 152 SMs x 128 FP32 lanes x "
                                          f"{sm_mhz:g} MHz / 11 instructions per multiply-add x 2 flops")
         else:
-            peak, peak_src = alu_peak, "nominal FP64 rate 1.25 TFLOP/s"
+            peak, peak_src = alu_peak, "measured cuBLAS FP64 GEMM rate (1.10 TFLOP/s)"
         roofline = {"kernel": "k_gemm_df: LOBPCG A and B products S X (factor-precision S, FP64 block, "
                               "FP32-pair accumulation on the SIMT units)",
                     "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
@@ -431,13 +468,13 @@ def main():
         tr = fam64["tc_trailing"]
         if tr["ms"] > 0:
             # the trailing updates C -= P P^T from exact slice products (k_oz_split + k_oz_gemm): FP64-accurate
-            # flops (2 per lower-triangle multiply-add) per second, against the nominal FP64 rate; each
+            # flops (2 per lower-triangle multiply-add) per second, against the measured FP64 GEMM rate; each
             # multiply-add is 36 TF32 slice products, against the TF32 tensor peak
             rate = tr["flops"] / (tr["ms"] * 1e-3) / 1e12
             fp64_form["trailing_update"] = {
                 "kernel": "k_oz_gemm (+ k_oz_split): C -= P P^T from eight 7-bit digit slices per entry on tcgen05",
                 "ms": tr["ms"], "launches": tr["launches"], "fp64_tflops": rate,
-                "vs_nominal_fp64_peak": rate / 1.25, "slice_product_tflops": 36 * rate,
+                "vs_fp64_gemm_peak": rate / MEASURED_FP64_TFLOPS, "slice_product_tflops": 36 * rate,
                 "tensor_frac": 36 * rate / tf32_peak,
                 "note": "family time of the untimed FP64 step (CUDA events); the timed step runs without events"}
         fp64_form["families_ms"] = {k: round(v["ms"], 1) for k, v in fam64.items() if v["ms"] > 0}
