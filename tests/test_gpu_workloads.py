@@ -2,8 +2,8 @@
 (tests/golden/config*_oracle.json, written by tests/golden/make_golden.py from
 oracle/ only).  Sampled outputs the oracle computed one by one: PCG
 iterations, adaptive rows per face, the indicator, and the top pair
-eigenvalues of the used columns.  The solution is checked through its true
-FP64 residual.
+eigenvalues of the used columns.  The solution is checked against a sparse
+direct solve (16^3) or through its residual in the oracle's own assembly (48^3).
 
 FP64 form: eigenvalues within 1e-4 relative, selected rows per face and PCG
 iterations within +-1 of the oracle.
@@ -70,12 +70,18 @@ def test_workload_against_oracle(B, index, precision, rtol_max, rtol_med, it_sla
     ctx.close()
     assert info.rel_residual <= 1e-8 and info.true_rel_residual <= 1.01e-8
     assert -1 <= info.iterations - g["pcg_iterations"] <= it_slack, (info.iterations, g["pcg_iterations"])
+    free = fe.free_dof_map(prob)[1]
     if index == 1:
         # the solution against a sparse direct solve of the oracle's assembly (4,624 dofs)
         import scipy.sparse.linalg as spla
-        free = fe.free_dof_map(prob)[1]
         ud = spla.spsolve(fe.assemble_global(prob).tocsc(), fe.load_vector(prob))
         assert np.linalg.norm(u[free] - ud) <= 1e-6 * np.linalg.norm(ud)
+    else:
+        # 345,744 dofs: the solution through its residual in the oracle's own assembly and load
+        # (a sparse direct solve of 3-D elasticity at this size takes minutes and tens of GB)
+        f_o = fe.load_vector(prob)
+        true_rel = np.linalg.norm(f_o - fe.assemble_global(prob) @ u[free]) / np.linalg.norm(f_o)
+        assert true_rel <= 1.01e-8, true_rel
     pairs = {(p["s"], p["t"]): p for p in rep["pairs"]}
     assert len(pairs) == len(g["pairs"])
     off = 0
