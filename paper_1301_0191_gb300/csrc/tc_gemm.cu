@@ -47,6 +47,7 @@
 
 #include "common.h"
 #include "tc_gemm.h"
+#include "oz_arith.h"
 
 namespace amb {
 
@@ -405,6 +406,7 @@ constexpr int kOzBTile = kOzTN * kTK * 4;                   // 8 KB
 constexpr int kOzBBytes = kOzSlices * kOzBTile;             // 64 KB
 constexpr int kOzSmemBytes = kOzBBufs * kOzBBytes + kOzAStages * kOzATile + 1024;
 static_assert(kOzSlices * kOzTN <= 512, "the level accumulators must fit TMEM");
+static_assert(kOzSlices == oz::kSlices, "one digit count for the split and the products");
 static_assert(kOzSmemBytes <= 227 * 1024, "shared memory");
 
 // kind::tf32 instruction descriptor for M = 128 and N columns
@@ -417,47 +419,6 @@ __device__ __forceinline__ void mma_tf32_idesc(uint32_t tacc, uint64_t a, uint64
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tacc),
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
       : "memory");
-}
-
-// (H 2^28 + L) 2^s rounded to the nearest double (ties to even), |H|, |L| <
-// 2^46, in 64-bit integer arithmetic: the exact value is written as
-// +-(a 2^28 + b) with a >= 0, 0 <= b < 2^28; its top 53 bits are rounded
-// once, however H and L cancel
-__device__ __forceinline__ double oz_round(int64_t H, int64_t L, int s) {
-  int64_t hi = H + (L >> 28);   // floor division: L = (L >> 28) 2^28 + lo
-  uint64_t lo = (uint64_t)(L & ((1ll << 28) - 1));
-  const bool neg = hi < 0;
-  uint64_t a;
-  if (neg) {
-    // -(hi 2^28 + lo) = (-hi - 1) 2^28 + (2^28 - lo), or -hi 2^28 when lo == 0
-    a = lo ? (uint64_t)(-hi - 1) : (uint64_t)(-hi);
-    lo = lo ? (1ull << 28) - lo : 0ull;
-  } else {
-    a = (uint64_t)hi;
-  }
-  if (a == 0 && lo == 0) return 0.0;
-  uint64_t m;
-  int nb;   // bit length of a 2^28 + lo
-  if (a < (1ull << 25)) {
-    m = (a << 28) | lo;   // exact: below 2^53
-    nb = 64 - __clzll((long long)m);
-    m <<= 53 - nb;
-  } else {
-    const int la = 64 - __clzll((long long)a);
-    const int sh = la - 25;   // 1 .. 22: the bits of lo below the 53 kept ones
-    nb = la + 28;
-    m = (a << (28 - sh)) | (lo >> sh);
-    const uint64_t rem = lo & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-    if (rem > half || (rem == half && (m & 1))) ++m;
-    if (m >> 53) {
-      m >>= 1;
-      ++nb;
-    }
-  }
-  const int E = nb - 1 + s;   // exponent of the result
-  if (E < -1022 || E > 1023) return ldexp(neg ? -(double)m : (double)m, E - 52);
-  const uint64_t bits = ((uint64_t)(E + 1023) << 52) | (m & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull);
-  return __longlong_as_double((long long)bits);
 }
 
 // FP64 source block (rows x cols; column form: (r, k) at src + r + k*ld,
@@ -490,45 +451,6 @@ __device__ __forceinline__ void oz_load_tile(const TcSplitDesc& x, int r0, int k
   }
 }
 
-// |x| as an ordered integer (the IEEE bit pattern without the sign)
-__device__ __forceinline__ uint64_t oz_absbits(double x) {
-  return (uint64_t)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFull;
-}
-
-// e with 2^(e-1) <= |x| < 2^e from the bits of |x| (x != 0)
-__device__ __forceinline__ int oz_exponent(uint64_t ab) {
-  const int bex = (int)(ab >> 52);
-  const uint64_t mant = (ab & 0xFFFFFFFFFFFFFull) | (bex ? (1ull << 52) : 0ull);
-  return (64 - __clzll((long long)mant)) + max(bex, 1) - 1075;
-}
-
-// the kOzSlices balanced base-128 digits of x 2^-e (|x| < 2^e): F = x 2^(56-e)
-// rounded to an integer (|F| < 2^56), least significant digit first, each
-// digit taken into (-64, 64] with a carry into the next
-__device__ __forceinline__ void oz_digits(double x, int e, float* dig) {
-  const uint64_t bits = (uint64_t)__double_as_longlong(x);
-  const uint64_t ab = bits & 0x7FFFFFFFFFFFFFFFull;
-  const int bex = (int)(ab >> 52);
-  const uint64_t mant = (ab & 0xFFFFFFFFFFFFFull) | (bex ? (1ull << 52) : 0ull);
-  const int sh = max(bex, 1) - 1075 + 56 - e;   // <= 3
-  int64_t F;
-  if (sh >= 0) F = (int64_t)(mant << sh);
-  else if (sh > -64) F = (int64_t)((mant + (1ull << (-sh - 1))) >> (-sh));
-  else F = 0;
-  const float sg = (bits >> 63) ? -1.f : 1.f;
-#pragma unroll
-  for (int p = kOzSlices - 1; p > 0; --p) {
-    int dd = (int)(F & 127);
-    F >>= 7;
-    if (dd > 64) {
-      dd -= 128;
-      F += 1;
-    }
-    dig[p] = sg * (float)dd;
-  }
-  dig[0] = sg * (float)F;   // 0 .. 128
-}
-
 __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, int64_t R, float* slab, int* ex) {
   __shared__ double t[32][kSplitRows + 1];   // [k][r]
   __shared__ int esh[kSplitRows];
@@ -542,11 +464,11 @@ __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, 
     oz_load_tile(x, r0, k0, tid, t);
     __syncthreads();
     if (tid < kSplitRows)
-      for (int kk = 0; kk < 32; ++kk) mx = max(mx, oz_absbits(t[kk][tid]));
+      for (int kk = 0; kk < 32; ++kk) mx = max(mx, oz::absbits(t[kk][tid]));
     __syncthreads();
   }
   if (tid < kSplitRows) {
-    const int e = mx ? oz_exponent(mx) : 0;
+    const int e = mx ? oz::exponent(mx) : 0;
     esh[tid] = e;
     ex[x.row0 + r0 + tid] = e;
   }
@@ -560,7 +482,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const TcSplitDesc* d, int kp, 
       const int e = esh[rr];
       float sl[4][kOzSlices];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) oz_digits(t[4 * g + u][rr], e, sl[u]);
+      for (int u = 0; u < 4; ++u) oz::digits(t[4 * g + u][rr], e, sl[u]);
 #pragma unroll
       for (int p = 0; p < kOzSlices; ++p)
         *reinterpret_cast<float4*>(slab + (p * R + x.row0 + r0 + rr) * (int64_t)kp + k0 + 4 * g) =
@@ -799,7 +721,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
           const int j = tj * kOzTN + h * 16 + q;
           // a tile without K steps (a triangular operand with no entries in
           // this chunk) has no accumulator data: its product is zero
-          v[h * 16 + q] = (kb < ke && j < d.n) ? oz_round(part[0][q], part[1][q], ei + ej[q] - 63) : 0.0;
+          v[h * 16 + q] = (kb < ke && j < d.n) ? oz::round_sum(part[0][q], part[1][q], ei + ej[q] - 63) : 0.0;
         }
       }
       // TMEM back to the MMA warp before the C traffic
