@@ -852,6 +852,9 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DiagDesc* descs, T* bas
     a[r][c] = (r >= c) ? (double)blk[r + (int64_t)c * d.ld] : 0.0;
   }
   __syncthreads();
+  // FP64 divisions are long instruction sequences on this GPU's slow FP64
+  // pipe: each pivot's reciprocal is formed once and multiplied
+  __shared__ double dinv[kNB];
   for (int c = 0; c < jb; ++c) {
     if (tid == 0) {
       double p = a[c][c];
@@ -863,10 +866,11 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DiagDesc* descs, T* bas
         p = 1.0;
       }
       a[c][c] = sqrt(p);
+      dinv[c] = 1.0 / a[c][c];
     }
     __syncthreads();
-    const double piv = a[c][c];
-    for (int r = c + 1 + tid; r < jb; r += blockDim.x) a[r][c] /= piv;
+    const double rpiv = dinv[c];
+    for (int r = c + 1 + tid; r < jb; r += blockDim.x) a[r][c] *= rpiv;
     __syncthreads();
     const int m = jb - c - 1;
     for (int idx = tid; idx < m * m; idx += blockDim.x) {
@@ -881,15 +885,14 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DiagDesc* descs, T* bas
   }
   // Inverse of the lower-triangular block by forward substitution, one
   // column per thread; entry (i, j), i > j, of the inverse is kept in the
-  // unused upper triangle a[j][i], its diagonal in dinv[].
-  __shared__ double dinv[kNB];
+  // unused upper triangle a[j][i], its diagonal in dinv[] (the reciprocals
+  // of the pivots, formed above).
   if (tid < jb) {
     const int j = tid;
-    dinv[j] = 1.0 / a[j][j];
     for (int i = j + 1; i < jb; ++i) {
       double s = a[i][j] * dinv[j];
       for (int l = j + 1; l < i; ++l) s += a[i][l] * a[j][l];
-      a[j][i] = -s / a[i][i];
+      a[j][i] = -s * dinv[i];
     }
   }
   __syncthreads();
