@@ -398,9 +398,9 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
 // Tiles are 128 x 64 (M x N): the eight accumulators of a tile fill the 512
 // TMEM columns.  Per K step of 32 the B rows of all slices (8 x 8 KB) sit in
 // one of two B buffers, and the A rows of one slice at a time (16 KB) in one
-// of three A stages: each slice tile is read from L2 once per K step.
+// of four A stages: each slice tile is read from L2 once per K step.
 
-constexpr int kOzTN = 64, kOzBBufs = 2, kOzAStages = 3;
+constexpr int kOzTN = 64, kOzBBufs = 2, kOzAStages = 4;
 constexpr int kOzATile = kTM * kTK * 4;                     // 16 KB
 constexpr int kOzBTile = kOzTN * kTK * 4;                   // 8 KB
 constexpr int kOzBBytes = kOzSlices * kOzBTile;             // 64 KB
