@@ -1442,7 +1442,26 @@ void Engine<T>::adapt_level(LevelData<T>& L) {
     }
     {
       FamTimer fo(st, &tm, AMB_FAM_LOBOP, timing());
-      gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+      if constexpr (std::is_same<T, double>::value) {
+        // FP64 form: S X from exact slice products on the tensor cores; the
+        // pair sides of one substructure share its S, split once per chunk
+        std::vector<TcGemm> tg;
+        std::vector<int> key;
+        tg.reserve(d.size());
+        key.reserve(d.size());
+        size_t i = 0;
+        for (int p = 0; p < np; ++p) {
+          if (!active[p]) continue;
+          for (int side = 0; side < 2; ++side, ++i) {
+            const GemmDesc& g = d[i];
+            tg.push_back(TcGemm{g.a, g.b, g.c, g.lda, g.ldb, g.ldc, g.m, g.n, g.k, 0, 1, 0});
+            key.push_back((int)qp[(size_t)p * Q_NPAIRF + (side ? Q_T : Q_S)]);
+          }
+        }
+        tc_gemm_f64(st, ring, tg, 1.0, 0.0, dptr<double>(L.S), Q, Q, dptr<int>(status), &key);
+      } else {
+        gemm_batched<V, T>(st, ring, d, G_TUNE, 1.0, 0.0, dptr<T>(L.S), Q, Q);
+      }
       std::vector<char> seen(L.ns, 0);
       for (size_t i = 0; i < d.size(); ++i) {
         const GemmDesc& g = d[i];

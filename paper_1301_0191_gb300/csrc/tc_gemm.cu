@@ -44,10 +44,11 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 
 #include "common.h"
-#include "tc_gemm.h"
 #include "oz_arith.h"
+#include "tc_gemm.h"
 
 namespace amb {
 
@@ -946,8 +947,12 @@ void run_oz(cudaStream_t st, DescRing& ring, const std::vector<TcSplitDesc>& sp,
 // C = beta C + alpha A B^T for every entry of d, K in chunks of kTcKMax: per
 // chunk the split descriptors (B rows, then the A row ranges that have
 // entries in the chunk) and the tile descriptors, handed to run(...)
+// akey (optional): products with the same key >= 0 share one dense A (same
+// offset, leading dimension, m, k and form), which is split once per chunk
 template <typename E, class Count, class Run>
-void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, Count count, Run run) {
+void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, Count count, Run run,
+                 const std::vector<int>* akey = nullptr) {
+  AMB_CHECK(!akey || akey->size() == d.size(), AMB_EINVAL, "tensor-core product keys do not match the products");
   constexpr int kp = kTcKMax;
   int kmax = 0;
   for (const auto& x : d) {
@@ -962,7 +967,9 @@ void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, C
     std::vector<int> prefix;
     int64_t rows = 0, tiles = 0;
     int maxr = 0;
-    for (const auto& x : d) {
+    std::unordered_map<int, int64_t> shared_arow;   // key -> slab row of its split A in this chunk
+    for (size_t di = 0; di < d.size(); ++di) {
+      const TcGemm& x = d[di];
       if (x.m <= 0 || x.n <= 0) continue;
       if (x.k <= 0) {
         // an empty sum: C = beta C, as one chunk with no K steps
@@ -970,6 +977,7 @@ void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, C
       } else if (k0 >= x.k) {
         continue;
       }
+      const int key = (akey && x.a_tri == 0) ? (*akey)[di] : -1;
       const int k1 = std::min(x.k, k0 + kp), kc = std::max(0, k1 - k0);
       // row ranges of A with entries in [k0, k1), and whether beta applies
       // (the chunk is the first that reaches those rows)
@@ -996,15 +1004,22 @@ void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, C
       for (int q = 0; q < nr; ++q) {
         const int r0 = rr[q][0], r1 = rr[q][1];
         const int mpad = pad_rows(r1 - r0);
-        const int64_t aoff = x.a_kmajor ? (int64_t)k0 + (int64_t)r0 * x.lda : (int64_t)r0 + (int64_t)k0 * x.lda;
-        sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(abase + x.a + aoff), rows, x.lda, r1 - r0, kc, mpad,
-                                 x.a_kmajor, x.a_tri, r0 - k0, 0});
-        TcDesc t{x.c + r0, rows, brow, r1 - r0, x.n, (kc + kTK - 1) / kTK * kTK, x.ldc, 0, x.a_tri, r0 - k0, rr[q][2]};
+        int64_t arow = rows;
+        auto hit = key >= 0 ? shared_arow.find(key) : shared_arow.end();
+        if (hit != shared_arow.end()) {
+          arow = hit->second;
+        } else {
+          const int64_t aoff = x.a_kmajor ? (int64_t)k0 + (int64_t)r0 * x.lda : (int64_t)r0 + (int64_t)k0 * x.lda;
+          sp.push_back(TcSplitDesc{reinterpret_cast<const float*>(abase + x.a + aoff), rows, x.lda, r1 - r0, kc, mpad,
+                                   x.a_kmajor, x.a_tri, r0 - k0, 0});
+          if (key >= 0) shared_arow[key] = rows;
+          rows += mpad;
+          maxr = std::max(maxr, mpad);
+        }
+        TcDesc t{x.c + r0, arow, brow, r1 - r0, x.n, (kc + kTK - 1) / kTK * kTK, x.ldc, 0, x.a_tri, r0 - k0, rr[q][2]};
         prefix.push_back((int)tiles);
         tiles += count(t);
         td.push_back(t);
-        rows += mpad;
-        maxr = std::max(maxr, mpad);
       }
     }
     if (td.empty()) break;
@@ -1042,12 +1057,13 @@ void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk
 }
 
 void tc_gemm_f64(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, double alpha, double beta,
-                 const double* abase, const double* bbase, double* cbase, int* status) {
+                 const double* abase, const double* bbase, double* cbase, int* status, const std::vector<int>* akey) {
   gemm_chunks(d, abase, bbase, oz_tile_count,
               [&](const std::vector<TcSplitDesc>& sp, const std::vector<TcDesc>& td, const std::vector<int>& prefix,
                   int64_t rows, int maxr, int64_t tiles) {
                 run_oz(st, ring, sp, td, prefix, rows, maxr, tiles, alpha, beta, cbase, status);
-              });
+              },
+              akey);
 }
 
 void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, float alpha, float beta,

@@ -80,8 +80,11 @@ void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk
 
 // FP64 form: C = beta C + alpha A B^T for every entry of d, as tc_gemm, with
 // the exact slice products of tc_syrk_lower_f64 per K chunk of kTcKMax
-// (each chunk rounded to FP64 once and added to C in FP64).
+// (each chunk rounded to FP64 once and added to C in FP64).  akey
+// (optional, one per entry): entries with the same key >= 0 share one dense
+// A, split once per chunk.
 void tc_gemm_f64(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, double alpha, double beta,
-                 const double* abase, const double* bbase, double* cbase, int* status);
+                 const double* abase, const double* bbase, double* cbase, int* status,
+                 const std::vector<int>* akey = nullptr);
 
 }  // namespace amb
