@@ -381,8 +381,10 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
 // ---------------------------------------------------------------- FP64 form: exact slice products
 //
 // C = beta C + alpha A B^T in FP64 accuracy on the TF32 tensor cores (the
-// Cholesky trailing updates, C lower and B = A, and the triangular-inverse
-// merges).  Every row r of an operand chunk (K <= 256) is scaled by 2^-e_r,
+// Cholesky trailing updates, C lower and B = A; the Cholesky strips and
+// panels; the triangular-inverse merges; the LOBPCG B products and the
+// triangular products of the pair preconditioner).  The integer arithmetic
+// is in oz_arith.h.  Every row r of an operand chunk (K <= 256) is scaled by 2^-e_r,
 // e_r the exponent of its largest entry (|X(r, k)| < 2^e_r), rounded to the
 // 56-bit integer F = X(r, k) 2^(56 - e_r) and written in balanced base-128
 // digits: X(r, k) = 2^e_r sum_p m_p 2^-7(p+1) up to 2^-57 of 2^e_r, with
