@@ -6,9 +6,11 @@
 #include "topology.h"
 
 #include <algorithm>
+#include <exception>
 #include <map>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <unordered_map>
 
 #include "amb.h"
@@ -17,6 +19,40 @@
 namespace amb {
 
 namespace {
+
+// f(t, i0, i1) on [0, n) cut into contiguous chunks, one per host thread (up
+// to 16, at least min_per_thread indices each, and no more than
+// scratch_budget / scratch_bytes threads when each needs scratch_bytes of its
+// own); t numbers the chunks.  Every index writes only its own outputs, so
+// the result does not depend on the split.  An exception in a chunk is
+// rethrown after all chunks end.
+template <class F>
+void parallel_chunks(int64_t n, int64_t min_per_thread, size_t scratch_bytes, F f) {
+  const unsigned hw = std::thread::hardware_concurrency();
+  int64_t nt = std::min<int64_t>(hw ? (int64_t)hw : 1, 16);
+  nt = std::min<int64_t>(nt, std::max<int64_t>(1, n / std::max<int64_t>(min_per_thread, 1)));
+  constexpr size_t kScratchBudget = size_t(256) << 20;
+  if (scratch_bytes > 0) nt = std::min<int64_t>(nt, std::max<int64_t>(1, (int64_t)(kScratchBudget / scratch_bytes)));
+  if (nt <= 1) {
+    f(0, (int64_t)0, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  std::vector<std::exception_ptr> err((size_t)nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int64_t i0 = n * t / nt, i1 = n * (t + 1) / nt;
+    th.emplace_back([&f, &err, t, i0, i1] {
+      try {
+        f((int)t, i0, i1);
+      } catch (...) {
+        err[(size_t)t] = std::current_exception();
+      }
+    });
+  }
+  for (auto& x : th) x.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
 
 enum { TAG_X0 = 1, TAG_X1 = 2, TAG_Y0 = 4, TAG_Y1 = 8, TAG_Z0 = 16, TAG_Z1 = 32 };
 
@@ -111,10 +147,22 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
     const int nb = __builtin_popcount((unsigned)N.tags[i] & 63u);
     return nb <= 3 && N.nsub(i) == (1 << (3 - nb));
   };
-  std::sort(order.begin(), order.end(), [&](int a, int b) {
-    if (rank[a] != rank[b]) return rank[a] < rank[b];
-    return N.tags[a] != N.tags[b] ? N.tags[a] < N.tags[b] : a < b;
-  });
+  // order by (rank, tags, node index): a stable counting sort of the nodes
+  // (already in index order) on the key rank * ntag + tags
+  int nrank = 0, ntag = 1;
+  for (int i : order) {
+    nrank = std::max(nrank, rank[i] + 1);
+    AMB_CHECK(N.tags[i] >= 0, AMB_EINVAL, "negative node tags");
+    ntag = std::max(ntag, N.tags[i] + 1);
+  }
+  auto counting_sort = [](std::vector<int>& v, int nkeys, auto key) {
+    std::vector<int> start((size_t)nkeys + 1, 0), out(v.size());
+    for (int i : v) ++start[key(i) + 1];
+    for (int k = 0; k < nkeys; ++k) start[k + 1] += start[k];
+    for (int i : v) out[start[key(i)]++] = i;
+    v.swap(out);
+  };
+  counting_sort(order, nrank * ntag, [&](int i) { return rank[i] * ntag + N.tags[i]; });
   for (size_t r = 0; r < order.size();) {
     size_t e = r + 1;
     while (e < order.size() && rank[order[r]] == rank[order[e]] && N.tags[order[r]] == N.tags[order[e]]) ++e;
@@ -126,7 +174,7 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
   std::vector<int> grp;
   for (int i = 0; i < nn; ++i)
     if (iface[i] && !corner[i]) grp.push_back(i);
-  std::stable_sort(grp.begin(), grp.end(), [&](int a, int b) { return rank[a] < rank[b]; });
+  counting_sort(grp, nrank, [&](int i) { return rank[i]; });
 
   L.n_dofs = N.n_dofs;
   L.objs.clear();
@@ -167,34 +215,74 @@ void classify(LevelTopo& L, const LevelNodes& N, int initial) {
   if (initial == AMB_CORNERS_EDGES_FACES)
     for (auto& f : faces) L.objs.push_back(average_object(N, OBJ_FACE, f.second));
 
-  // substructure dof lists: interior, delta, corner (each sorted by level dof)
+  // substructure dof lists: interior, delta, corner (each sorted by level
+  // dof), gathered in node order over node ranges in parallel: counts per
+  // (range, kind, substructure), then every range fills its own slots
   L.subs.assign(L.n_subs, SubTopo());
-  std::vector<std::vector<int64_t>> inter(L.n_subs), delta(L.n_subs), crn(L.n_subs);
-  for (int i = 0; i < nn; ++i) {
-    if (N.ndof(i) == 0) continue;
-    for (int k = 0; k < N.nsub(i); ++k) {
-      const int s = N.sub(i)[k];
-      auto& dst = !iface[i] ? inter[s] : (corner[i] ? crn[s] : delta[s]);
-      dst.insert(dst.end(), N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1]);
+  const int ns = L.n_subs;
+  std::vector<std::vector<int64_t>> lists[3];   // interior, delta, corner
+  for (auto& l : lists) l.assign(ns, {});
+  auto kind_of = [&](int i) { return !iface[i] ? 0 : (corner[i] ? 2 : 1); };
+  std::vector<std::vector<int64_t>> kcnt(16, std::vector<int64_t>());
+  int nchunks = 0;
+  parallel_chunks(nn, 1 << 14, 0, [&](int t, int64_t i0, int64_t i1) {
+    std::vector<int64_t>& c = kcnt[t];
+    c.assign((size_t)3 * ns, 0);
+    for (int64_t i = i0; i < i1; ++i) {
+      if (N.ndof((int)i) == 0) continue;
+      const int kd = kind_of((int)i);
+      for (int k = 0; k < N.nsub((int)i); ++k) c[(size_t)kd * ns + N.sub((int)i)[k]] += N.ndof((int)i);
     }
-  }
+  });
+  for (int t = 0; t < 16; ++t)
+    if (!kcnt[t].empty()) nchunks = t + 1;
+  std::vector<int64_t> base((size_t)nchunks * 3 * ns, 0);   // start of chunk t in each list
+  for (int kd = 0; kd < 3; ++kd)
+    for (int sb = 0; sb < ns; ++sb) {
+      int64_t run = 0;
+      for (int t = 0; t < nchunks; ++t) {
+        base[((size_t)t * 3 + kd) * ns + sb] = run;
+        run += kcnt[t][(size_t)kd * ns + sb];
+      }
+      lists[kd][sb].resize(run);
+    }
+  parallel_chunks(nn, 1 << 14, 0, [&](int t, int64_t i0, int64_t i1) {
+    int64_t* pos = base.data() + (size_t)t * 3 * ns;
+    for (int64_t i = i0; i < i1; ++i) {
+      if (N.ndof((int)i) == 0) continue;
+      const int kd = kind_of((int)i);
+      for (int k = 0; k < N.nsub((int)i); ++k) {
+        const int sb = N.sub((int)i)[k];
+        int64_t& at = pos[(size_t)kd * ns + sb];
+        std::copy(N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1], lists[kd][sb].begin() + at);
+        at += N.ndof((int)i);
+      }
+    }
+  });
+  std::vector<std::vector<int64_t>>& inter = lists[0];
+  std::vector<std::vector<int64_t>>& delta = lists[1];
+  std::vector<std::vector<int64_t>>& crn = lists[2];
   L.corner_dofs.clear();
   for (int i = 0; i < nn; ++i)
     if (corner[i]) L.corner_dofs.insert(L.corner_dofs.end(), N.dofs.begin() + N.doff[i], N.dofs.begin() + N.doff[i + 1]);
   std::sort(L.corner_dofs.begin(), L.corner_dofs.end());
-  for (int s = 0; s < L.n_subs; ++s) {
-    std::sort(inter[s].begin(), inter[s].end());
-    std::sort(delta[s].begin(), delta[s].end());
-    std::sort(crn[s].begin(), crn[s].end());
-    SubTopo& sb = L.subs[s];
-    sb.n_i = (int)inter[s].size();
-    sb.n_g = (int)(delta[s].size() + crn[s].size());
-    sb.n_crn = (int)crn[s].size();
-    sb.dofs.reserve(inter[s].size() + sb.n_g);
-    sb.dofs = inter[s];
-    sb.dofs.insert(sb.dofs.end(), delta[s].begin(), delta[s].end());
-    sb.dofs.insert(sb.dofs.end(), crn[s].begin(), crn[s].end());
-  }
+  parallel_chunks(L.n_subs, 4, 0, [&](int, int64_t s0, int64_t s1) {
+    for (int64_t s = s0; s < s1; ++s) {
+      // in node order the lists are sorted already when a node's dofs are
+      // consecutive and increasing with the node (level 1, and the coarse
+      // dofs of the objects of a level below)
+      for (auto* v : {&inter[s], &delta[s], &crn[s]})
+        if (!std::is_sorted(v->begin(), v->end())) std::sort(v->begin(), v->end());
+      SubTopo& sb = L.subs[s];
+      sb.n_i = (int)inter[s].size();
+      sb.n_g = (int)(delta[s].size() + crn[s].size());
+      sb.n_crn = (int)crn[s].size();
+      sb.dofs.reserve(inter[s].size() + sb.n_g);
+      sb.dofs = inter[s];
+      sb.dofs.insert(sb.dofs.end(), delta[s].begin(), delta[s].end());
+      sb.dofs.insert(sb.dofs.end(), crn[s].begin(), crn[s].end());
+    }
+  });
   // global interface numbering (increasing level dof) and owners (increasing
   // substructure), by counting over the level's dof space
   std::vector<int> cnt(N.n_dofs + 1, 0);
@@ -295,10 +383,12 @@ void number_coarse(LevelTopo& L) {
     sb.rc.insert(sb.rc.end(), others.begin(), others.end());
     for (int l = 0; l < sb.n_g; ++l) gpos[sb.dofs[sb.n_i + l]] = -1;
   }
-  // pair data
+  // pair data (pairs in parallel, scratch over the dof space per thread)
+  parallel_chunks((int64_t)L.pairs.size(), 16, (size_t)2 * L.n_dofs * sizeof(int), [&](int, int64_t p0, int64_t p1) {
   std::vector<int> pb(L.n_dofs, -1), fent(L.n_dofs, -1);
   std::vector<std::pair<int64_t, int>> adofs;
-  for (auto& p : L.pairs) {
+  for (int64_t pi = p0; pi < p1; ++pi) {
+    PairTopo& p = L.pairs[pi];
     const SubTopo& a = L.subs[p.s];
     const SubTopo& b = L.subs[p.t];
     for (int l = 0; l < b.n_g; ++l) pb[b.dofs[b.n_i + l]] = l;
@@ -352,6 +442,7 @@ void number_coarse(LevelTopo& L) {
     for (int64_t c : a.rc) p.cmap_s.push_back(pc[c]);
     for (int64_t c : b.rc) p.cmap_t.push_back(pc[c]);
   }
+  });
   check_topology(L);
 }
 
@@ -489,52 +580,70 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
   const int64_t nnx = nx + 1, nny = ny + 1, nnz = nz + 1;
   const int64_t nn = nnx * nny * nnz;
   const int64_t nel = (int64_t)nx * ny * nz;
-  for (int64_t e = 0; e < nel; ++e)
-    AMB_CHECK(elem_to_sub[e] >= 0 && elem_to_sub[e] < n_subs, AMB_EINVAL, "elem_to_sub out of range");
+  parallel_chunks(nel, 1 << 16, 0, [&](int, int64_t e0, int64_t e1) {
+    for (int64_t e = e0; e < e1; ++e)
+      AMB_CHECK(elem_to_sub[e] >= 0 && elem_to_sub[e] < n_subs, AMB_EINVAL, "elem_to_sub out of range");
+  });
+  // sharing set of node n: the substructures of the (up to 8) elements around it, sorted
+  auto sharing = [&](int64_t n, int* set) {
+    const int64_t i = n % nnx, j = (n / nnx) % nny, k = n / (nnx * nny);
+    int c = 0;
+    for (int64_t ek = k - 1; ek <= k; ++ek) {
+      if (ek < 0 || ek >= nz) continue;
+      for (int64_t ej = j - 1; ej <= j; ++ej) {
+        if (ej < 0 || ej >= ny) continue;
+        for (int64_t ei = i - 1; ei <= i; ++ei) {
+          if (ei < 0 || ei >= nx) continue;
+          const int sb = elem_to_sub[ei + nx * (ej + ny * ek)];
+          if (std::find(set, set + c, sb) == set + c) set[c++] = sb;
+        }
+      }
+    }
+    for (int a = 1; a < c; ++a)   // insertion sort of at most 8 ids
+      for (int b = a; b > 0 && set[b - 1] > set[b]; --b) std::swap(set[b - 1], set[b]);
+    return c;
+  };
+  // CSR of the nodes in two passes over node ranges: sizes, then contents
   LevelNodes N;
   N.n_dofs = nn * dpn;
   N.tags.assign(nn, 0);
   N.eligible.assign(nn, 1);
-  N.soff.reserve(nn + 1);
-  N.subs.reserve(nn + nn / 4);
-  N.doff.reserve(nn + 1);
-  N.dofs.reserve(nn * dpn);
-  N.comps.reserve(nn * dpn);
-  for (int64_t k = 0; k < nnz; ++k)
-    for (int64_t j = 0; j < nny; ++j)
-      for (int64_t i = 0; i < nnx; ++i) {
-        const int64_t n = i + nnx * (j + nny * k);
-        // sharing set: substructures of the (up to 8) elements around the node
-        int set[8], c = 0;
-        for (int64_t ek = k - 1; ek <= k; ++ek) {
-          if (ek < 0 || ek >= nz) continue;
-          for (int64_t ej = j - 1; ej <= j; ++ej) {
-            if (ej < 0 || ej >= ny) continue;
-            for (int64_t ei = i - 1; ei <= i; ++ei) {
-              if (ei < 0 || ei >= nx) continue;
-              const int s = elem_to_sub[ei + nx * (ej + ny * ek)];
-              if (std::find(set, set + c, s) == set + c) set[c++] = s;
-            }
-          }
-        }
-        std::sort(set, set + c);
-        N.subs.insert(N.subs.end(), set, set + c);
-        N.soff.push_back((int)N.subs.size());
-        int t = 0;
-        if (i == 0) t |= TAG_X0;
-        if (i == nx) t |= TAG_X1;
-        if (j == 0) t |= TAG_Y0;
-        if (j == ny) t |= TAG_Y1;
-        if (k == 0) t |= TAG_Z0;
-        if (k == nz) t |= TAG_Z1;
-        N.tags[n] = t;
-        if (!dirichlet[n])
-          for (int q = 0; q < dpn; ++q) {
-            N.dofs.push_back(n * dpn + q);
-            N.comps.push_back(q);
-          }
-        N.doff.push_back((int64_t)N.dofs.size());
+  N.soff.assign(nn + 1, 0);
+  N.doff.assign(nn + 1, 0);
+  parallel_chunks(nn, 1 << 14, 0, [&](int, int64_t n0, int64_t n1) {
+    int set[8];
+    for (int64_t n = n0; n < n1; ++n) {
+      N.soff[n + 1] = sharing(n, set);
+      N.doff[n + 1] = dirichlet[n] ? 0 : dpn;
+    }
+  });
+  for (int64_t n = 0; n < nn; ++n) {
+    N.soff[n + 1] += N.soff[n];
+    N.doff[n + 1] += N.doff[n];
+  }
+  N.subs.resize(N.soff[nn]);
+  N.dofs.resize(N.doff[nn]);
+  N.comps.resize(N.doff[nn]);
+  parallel_chunks(nn, 1 << 14, 0, [&](int, int64_t n0, int64_t n1) {
+    int set[8];
+    for (int64_t n = n0; n < n1; ++n) {
+      const int c = sharing(n, set);
+      std::copy(set, set + c, N.subs.begin() + N.soff[n]);
+      const int64_t i = n % nnx, j = (n / nnx) % nny, k = n / (nnx * nny);
+      int t = 0;
+      if (i == 0) t |= TAG_X0;
+      if (i == nx) t |= TAG_X1;
+      if (j == 0) t |= TAG_Y0;
+      if (j == ny) t |= TAG_Y1;
+      if (k == 0) t |= TAG_Z0;
+      if (k == nz) t |= TAG_Z1;
+      N.tags[n] = t;
+      for (int64_t q = N.doff[n]; q < N.doff[n + 1]; ++q) {
+        N.dofs[q] = n * dpn + (q - N.doff[n]);
+        N.comps[q] = (int)(q - N.doff[n]);
       }
+    }
+  });
   LevelTopo L;
   L.n_subs = n_subs;
   classify(L, N, initial);
@@ -544,7 +653,6 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
   // element -> local index in its substructure, -1 for Dirichlet dofs
   const int nd = 8 * dpn;
   elem_local.assign(nel * nd, -1);
-  std::vector<int32_t> loc(nn * dpn, -1);
   std::vector<int64_t> eoff(n_subs + 1, 0), elems(nel);
   for (int64_t e = 0; e < nel; ++e) ++eoff[elem_to_sub[e] + 1];
   for (int s = 0; s < n_subs; ++s) eoff[s + 1] += eoff[s];
@@ -552,20 +660,24 @@ LevelTopo build_level_one(int nx, int ny, int nz, int dpn, const uint8_t* dirich
     std::vector<int64_t> cur(eoff.begin(), eoff.end() - 1);
     for (int64_t e = 0; e < nel; ++e) elems[cur[elem_to_sub[e]]++] = e;
   }
-  for (int s = 0; s < n_subs; ++s) {
-    const SubTopo& sb = L.subs[s];
-    for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = (int32_t)q;
-    for (int64_t x = eoff[s]; x < eoff[s + 1]; ++x) {
-      const int64_t e = elems[x];
-      const int64_t i = e % nx, j = (e / nx) % ny, k = e / ((int64_t)nx * ny);
-      for (int a = 0; a < 8; ++a) {
-        const int64_t n = (i + (a & 1)) + nnx * ((j + ((a >> 1) & 1)) + nny * (k + ((a >> 2) & 1)));
-        if (dirichlet[n]) continue;
-        for (int c = 0; c < dpn; ++c) elem_local[e * nd + a * dpn + c] = loc[n * dpn + c];
+  // substructures in parallel, each thread with its own dof -> position scratch
+  parallel_chunks(n_subs, 2, (size_t)nn * dpn * sizeof(int32_t), [&](int, int64_t s0, int64_t s1) {
+    std::vector<int32_t> loc(nn * dpn, -1);
+    for (int64_t s = s0; s < s1; ++s) {
+      const SubTopo& sb = L.subs[s];
+      for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = (int32_t)q;
+      for (int64_t x = eoff[s]; x < eoff[s + 1]; ++x) {
+        const int64_t e = elems[x];
+        const int64_t i = e % nx, j = (e / nx) % ny, k = e / ((int64_t)nx * ny);
+        for (int a = 0; a < 8; ++a) {
+          const int64_t n = (i + (a & 1)) + nnx * ((j + ((a >> 1) & 1)) + nny * (k + ((a >> 2) & 1)));
+          if (dirichlet[n]) continue;
+          for (int c = 0; c < dpn; ++c) elem_local[e * nd + a * dpn + c] = loc[n * dpn + c];
+        }
       }
+      for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = -1;
     }
-    for (size_t q = 0; q < sb.dofs.size(); ++q) loc[sb.dofs[q]] = -1;
-  }
+  });
   return L;
 }
 
