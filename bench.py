@@ -32,9 +32,9 @@ import amb_inputs as ai  # noqa: E402
 METRIC = "adaptive-BDDC setup+solve s to 1e-8 rel. residual; Schur-apply % of roofline"
 WORKLOAD = "elasticity48_4x4x4_lognormal"
 # DRAM bytes per 128 x 128 output tile of the tensor-core trailing update, from one ncu capture of that kernel
-# on the 2x2x2 corner block of the 48^3 workload (one launch: 1,036,088,832 bytes over 7240 tiles; None when
-# the kernel has changed since)
-TC_TRAFFIC_PER_TILE = 1036088832 / 7240
+# on the 2x2x2 corner block of the 48^3 workload (its first launch, the update after the first 256 columns:
+# 699.54 MB read + 536.97 MB written over 9424 tiles; None when the kernel has changed since)
+TC_TRAFFIC_PER_TILE = 1236.51e6 / 9424
 TC_OUTER, TC_TILE = 256, 128
 # DRAM bytes (read + write) of one B apply of the LOBPCG operator products on the 48^3 workload, from one
 # 1-pass ncu capture of the timed step (None when the kernel has changed since)
@@ -394,7 +394,7 @@ def main():
                     if TC_TRAFFIC_PER_TILE and tc["launches"] >= 2 else None,
                     "traffic_note": "k_tc_syrk DRAM bytes per launch (each update = one k_tc_split + one k_tc_syrk "
                                     "launch): bytes per 128x128 tile from one ncu capture of one launch on the 2x2x2 "
-                                    "corner block (7240 tiles) x this step's tiles / updates; the split pass is not "
+                                    "corner block (9424 tiles) x this step's tiles / updates; the split pass is not "
                                     "included",
                     "algorithmic_bytes_per_tile": 2 * 4 * TC_TILE * TC_TILE,
                     "launches": tc["launches"], "ms": tc["ms"],
