@@ -26,6 +26,14 @@
  *    legacy default stream); calls return after that stream has finished
  *    the call's work, so outputs are ready on return.
  *  - A context is not thread-safe: use one context per host thread.
+ *  - Beside the contexts' own memory, each host thread that calls the
+ *    library keeps device workspaces for its tensor-core products (the
+ *    operand slabs of the current Cholesky panel or product chunk; in the
+ *    FP64 form eight FP32 digit slices per operand entry, 3.4 GB for the
+ *    48^3 workload's largest update).  They grow to the largest need seen,
+ *    are reused by later calls of the same thread and freed when the thread
+ *    ends.  The set-up's host combinatorics run on up to 16 threads of
+ *    their own, which end before the call returns.
  */
 #ifndef AMB_H
 #define AMB_H
