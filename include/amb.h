@@ -33,7 +33,9 @@
  *    48^3 workload's largest update).  They grow to the largest need seen,
  *    are reused by later calls of the same thread and freed when the thread
  *    ends.  The set-up's host combinatorics run on up to 16 threads of
- *    their own, which end before the call returns.
+ *    their own, which end before the call returns; the environment variable
+ *    AMB_HOST_THREADS (read once) caps them (1: the calling thread only).
+ *    Their results do not depend on the number of threads.
  */
 #ifndef AMB_H
 #define AMB_H

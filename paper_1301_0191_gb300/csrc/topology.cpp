@@ -6,6 +6,7 @@
 #include "topology.h"
 
 #include <algorithm>
+#include <cstdlib>
 #include <exception>
 #include <map>
 #include <stdexcept>
@@ -21,15 +22,26 @@ namespace amb {
 namespace {
 
 // f(t, i0, i1) on [0, n) cut into contiguous chunks, one per host thread (up
-// to 16, at least min_per_thread indices each, and no more than
+// to 16 and to AMB_HOST_THREADS, at least min_per_thread indices each, and no more than
 // scratch_budget / scratch_bytes threads when each needs scratch_bytes of its
 // own); t numbers the chunks.  Every index writes only its own outputs, so
 // the result does not depend on the split.  An exception in a chunk is
 // rethrown after all chunks end.
+// AMB_HOST_THREADS (environment, read once) caps the thread count; 1 runs
+// everything on the calling thread.
+int host_thread_cap() {
+  static const int cap = [] {
+    const char* v = std::getenv("AMB_HOST_THREADS");
+    const int n = v ? std::atoi(v) : 0;
+    return n > 0 ? n : 16;
+  }();
+  return cap;
+}
+
 template <class F>
 void parallel_chunks(int64_t n, int64_t min_per_thread, size_t scratch_bytes, F f) {
   const unsigned hw = std::thread::hardware_concurrency();
-  int64_t nt = std::min<int64_t>(hw ? (int64_t)hw : 1, 16);
+  int64_t nt = std::min<int64_t>(hw ? (int64_t)hw : 1, std::min(16, host_thread_cap()));
   nt = std::min<int64_t>(nt, std::max<int64_t>(1, n / std::max<int64_t>(min_per_thread, 1)));
   constexpr size_t kScratchBudget = size_t(256) << 20;
   if (scratch_bytes > 0) nt = std::min<int64_t>(nt, std::max<int64_t>(1, (int64_t)(kScratchBudget / scratch_bytes)));
