@@ -1,4 +1,5 @@
-// Tensor-core (tcgen05, 3xTF32) kernels of the FP32 form (tc_gemm.cu).
+// Tensor-core (tcgen05) kernels (tc_gemm.cu): 3xTF32 products of the FP32 form
+// and exact slice products of the FP64 form.
 #pragma once
 
 #include <vector>
@@ -73,7 +74,8 @@ void tc_gemm(cudaStream_t st, DescRing& ring, const std::vector<TcGemm>& d, floa
 // kOzSlices integer slices of 7 bits (exact in TF32); the products of slices
 // p and q with p + q < kOzSlices are summed per level p + q in FP32 TMEM
 // accumulators, where every partial sum is an integer below 2^24 and hence
-// exact; the levels are combined in FP32 pairs and added to C in FP64.
+// exact; the levels are combined exactly in 64-bit integers, rounded to FP64
+// once and added to C with one FP64 multiply-add.
 constexpr int kOzSlices = 8;
 void tc_syrk_lower_f64(cudaStream_t st, DescRing& ring, const std::vector<TcSyrk>& d, double alpha, double beta,
                        double* base, int* status);

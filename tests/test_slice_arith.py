@@ -114,3 +114,34 @@ def test_single_rounding_of_the_exact_level_sum(harness):
         else:
             # below the normal range the kernel rounds to 53 bits and then ldexp to the subnormal grid
             assert abs(Fraction(got) - exact) <= Fraction(2) ** -1074, (H, L, s, got)
+
+
+def test_slice_products_match_exact_products_within_the_fp64_bound(harness):
+    """C = A B^T formed the way the slice GEMM forms it (per-row exponents, digit slices, exact level
+    sums over K <= 256, one rounding), against the exact rational products.  Per term the digit
+    truncation of both operands (2^-57 of 2^e each) and the dropped levels p + q >= 8 leave at most
+    2^-54 2^(e_a + e_b), with 2^e <= 2 max|row|; the final rounding adds half an ulp:
+    |C - AB^T| <= K 2^-52 max|A_i| max|B_j| + 2^-53 |AB^T|."""
+    rng = random.Random(13)
+    for it, (m, n, k) in enumerate([(5, 4, 1), (6, 5, 7), (4, 4, 64), (3, 3, 256), (4, 2, 256)]):
+        def row():
+            scale = 10.0 ** rng.randint(-6, 6)
+            r = [rng.gauss(0, 1) * scale * (10.0 ** rng.randint(-8, 0) if rng.random() < 0.3 else 1.0) for _ in range(k)]
+            if rng.random() < 0.2:
+                r[rng.randrange(k)] = 0.0
+            return r
+        A = [row() for _ in range(m)]
+        B = [row() for _ in range(n)]
+        if it == 2:   # cancellation: B's first row orthogonal-ish to A's first row
+            B[0] = [-x for x in A[0]]
+        text = f"G {m} {n} {k}\n" + "\n".join(" ".join(f"{_bits(x):016x}" for x in r) for r in A + B) + "\n"
+        out = [l for l in _run(harness, text) if l]
+        assert len(out) == m
+        for i in range(m):
+            vals = [_double(int(h, 16)) for h in out[i].split()]
+            assert len(vals) == n
+            for j in range(n):
+                exact = sum(Fraction(a) * Fraction(b) for a, b in zip(A[i], B[j]))
+                bound = k * Fraction(2) ** -52 * Fraction(max(abs(x) for x in A[i])) * \
+                    Fraction(max(abs(x) for x in B[j])) + Fraction(2) ** -53 * abs(exact)
+                assert abs(Fraction(vals[j]) - exact) <= bound, (it, i, j, vals[j], float(exact))
