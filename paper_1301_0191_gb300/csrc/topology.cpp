@@ -26,7 +26,8 @@ namespace {
 // scratch_budget / scratch_bytes threads when each needs scratch_bytes of its
 // own); t numbers the chunks.  Every index writes only its own outputs, so
 // the result does not depend on the split.  An exception in a chunk is
-// rethrown after all chunks end.
+// rethrown after all chunks end; chunks whose thread cannot be started run
+// on the calling thread.
 // AMB_HOST_THREADS (environment, read once) caps the thread count; 1 runs
 // everything on the calling thread.
 int host_thread_cap() {
@@ -50,17 +51,22 @@ void parallel_chunks(int64_t n, int64_t min_per_thread, size_t scratch_bytes, F 
     return;
   }
   std::vector<std::thread> th;
+  th.reserve((size_t)nt);
   std::vector<std::exception_ptr> err((size_t)nt);
-  for (int64_t t = 0; t < nt; ++t) {
-    const int64_t i0 = n * t / nt, i1 = n * (t + 1) / nt;
-    th.emplace_back([&f, &err, t, i0, i1] {
-      try {
-        f((int)t, i0, i1);
-      } catch (...) {
-        err[(size_t)t] = std::current_exception();
-      }
-    });
+  auto chunk = [&f, &err, n, nt](int64_t t) {
+    try {
+      f((int)t, n * t / nt, n * (t + 1) / nt);
+    } catch (...) {
+      err[(size_t)t] = std::current_exception();
+    }
+  };
+  int64_t started = 0;
+  try {
+    for (; started < nt; ++started) th.emplace_back(chunk, started);
+  } catch (...) {
+    // no thread could be started: the calling thread runs the remaining chunks
   }
+  for (int64_t t = started; t < nt; ++t) chunk(t);
   for (auto& x : th) x.join();
   for (auto& e : err)
     if (e) std::rethrow_exception(e);
