@@ -963,6 +963,19 @@ void gemm_chunks(const std::vector<TcGemm>& d, const E* abase, const E* bbase, C
     AMB_CHECK(x.a_tri != 2 || x.m <= x.k, AMB_EINVAL, "upper-triangular tensor-core operand with m > k");
     if (x.m > 0 && x.n > 0) kmax = std::max(kmax, x.k);
   }
+  if (akey) {
+    // a shared split is only valid for products whose A is the same matrix
+    std::unordered_map<int, size_t> first;
+    for (size_t di = 0; di < d.size(); ++di) {
+      const int key = (*akey)[di];
+      const TcGemm& x = d[di];
+      if (key < 0 || x.a_tri != 0 || x.m <= 0 || x.n <= 0) continue;
+      auto it = first.emplace(key, di).first;
+      const TcGemm& y = d[it->second];
+      AMB_CHECK(x.a == y.a && x.lda == y.lda && x.m == y.m && x.k == y.k && x.a_kmajor == y.a_kmajor, AMB_EINVAL,
+                "tensor-core products with one key have different A operands");
+    }
+  }
   for (int k0 = 0; k0 < kmax || (k0 == 0 && kmax == 0); k0 += kp) {
     std::vector<TcSplitDesc> sp;
     std::vector<TcDesc> td;
