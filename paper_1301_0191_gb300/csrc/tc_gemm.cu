@@ -37,8 +37,9 @@
 // accurate as an FP32 FMA chain (rms 2.4e-8 vs 2.8e-8 relative to sum |terms|
 // for random signs, 4.0e-7 vs 2.5e-7 for positive terms, K = 256).  Every wait
 // is bounded: a wait that runs out sets AMB_ETIMEOUT in the status word and
-// raises a CTA-wide abort flag; every role then leaves its loop and TMEM is
-// released.
+// raises a CTA-wide abort flag; every role then leaves its loop, the TMA
+// copies and MMAs already started are waited for (bounded again), and TMEM
+// is released.
 #include <cuda.h>
 
 #include <algorithm>
@@ -179,6 +180,32 @@ __device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatil
   return false;
 }
 
+// bounded wait without the abort test, for the drain after an abort
+__device__ __forceinline__ void drain_wait(uint32_t bar, uint32_t parity, int* status) {
+  for (long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try(bar, parity)) return;
+    if (it > 4096) __nanosleep(64);
+  }
+  if (status) atomicCAS(status, 0, AMB_ETIMEOUT);
+}
+
+// After an abort the CTA must not exit while TMA copies it started still
+// write its shared memory: wait for the last phase the producer started on
+// each of the n stage barriers (issued loads so far; load i went to stage
+// i % n as its use i / n).
+__device__ __forceinline__ void drain_loads(const uint64_t* full, int n, uint32_t issued, int* status) {
+  for (int s = 0; s < n; ++s)
+    if (issued > (uint32_t)s) drain_wait(smem_u32(&full[s]), ((issued - 1 - (uint32_t)s) / (uint32_t)n) & 1u, status);
+}
+
+// ... nor while MMAs it issued still run: one more commit, to its own
+// barrier, arrives once all of them have completed
+__device__ __forceinline__ void drain_mmas(uint64_t* done, int* status) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(done))
+               : "memory");
+  drain_wait(smem_u32(done), 0, status);
+}
+
 __device__ __forceinline__ void tile_coords(const TcTileArgs& g, int tile, TcDesc& d, int& ti, int& tj) {
   int lo = 0, hi = g.ndesc - 1;
   while (lo < hi) {
@@ -213,7 +240,7 @@ __device__ __forceinline__ void tile_krange(const TcDesc& d, int ti, int& kb, in
 __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUtensorMap map_h,
                                                    const __grid_constant__ CUtensorMap map_l, TcTileArgs g) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull, tempty;
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], tfull, tempty, mdone;
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_sh;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -231,6 +258,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfull)), "r"(1) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty)), "r"(4) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mdone)), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_h) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_l) : "memory");
@@ -264,6 +292,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
           tma_load_2d(sb + 3 * kTileBytes, &map_l, kt * kTK, yb, fb);
         }
       }
+      if (abort_sh) drain_loads(full, kStages, it, g.status);
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
@@ -300,6 +329,7 @@ __global__ void __launch_bounds__(192, 1) k_tc_syrk(const __grid_constant__ CUte
                          smem_u32(&tfull))
                      : "memory");
       }
+      if (abort_sh) drain_mmas(&mdone, g.status);
     }
   } else {
     // ---------------------------------------------------------------- epilogue (warps 2..5)
@@ -532,7 +562,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
                                                    const __grid_constant__ CUtensorMap map_b, OzArgs ga) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t bfull[kOzBBufs], bempty[kOzBBufs], afull[kOzAStages], aempty[kOzAStages], tfull,
-      tempty;
+      tempty, mdone;
   __shared__ uint32_t tbase;
   __shared__ volatile int abort_sh;
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -558,6 +588,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tfull)), "r"(1) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty)), "r"(4) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mdone)), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_a) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&map_b) : "memory");
@@ -601,6 +632,10 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
             tma_load_2d(smem_u32(abuf + sa * kOzATile), &map_a, kt * kTK, (int)(p * R + ya), afb);
           }
         }
+      }
+      if (abort_sh) {
+        drain_loads(bfull, kOzBBufs, ib, g.status);
+        drain_loads(afull, kOzAStages, ia, g.status);
       }
     }
   } else if (warp == 1) {
@@ -662,6 +697,7 @@ __global__ void __launch_bounds__(192, 1) k_oz_gemm(const __grid_constant__ CUte
                          smem_u32(&tfull))
                      : "memory");
       }
+      if (abort_sh) drain_mmas(&mdone, g.status);
     }
   } else {
     // ---------------------------------------------------------------- epilogue (warps 2..5)
