@@ -157,8 +157,10 @@ class Clocks:
 
 # ---------------------------------------------------------------- oracle sample
 # PCG iterations of the oracle on the full workloads (tests/golden for 48^3; the 96^3 three-level workload is
-# too large for the whole oracle, so its estimate uses the library's FP64-form count, 30)
-ORACLE_ITS = {"c2": 37, "c3": 30}
+# too large for the whole oracle, so its estimate uses the library's FP64-form count, 30; so does the 64^3
+# Poisson workload of the gradient, whose stored oracle run solved to 1e-12 for the gradient check)
+ORACLE_ITS = {"c2": 37, "c3": 30, "c4": 30}
+CONFIG_INDEX = {"c2": 2, "c2block": 2, "c3": 3, "c4": 4}
 
 
 def oracle_sample(prob, its_full=37):
@@ -210,10 +212,11 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-form", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2block", "c3"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2block", "c3", "c4"],
                     help="c2: the 48^3 elasticity workload; c3: the 96^3 Poisson workload on 512 irregular "
-                         "boxes, three levels; c2block: a corner block of the c2 substructures (same shapes; "
-                         "2x1x1 holds ~0.5 GB on the device), for profiler captures")
+                         "boxes, three levels; c4: the 64^3 Poisson workload on a Gaussian random field, with "
+                         "the compliance gradient (amb_grad) in every step; c2block: a corner block of the c2 "
+                         "substructures (same shapes; 2x1x1 holds ~0.5 GB on the device), for profiler captures")
     ap.add_argument("--block", default="2,1,1", help="substructures per axis of the c2block workload")
     ap.add_argument("--profile", action="store_true",
                     help="warm-up + timed steps only (no e2e, family timing, Schur sweep or baselines)")
@@ -226,15 +229,17 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    prob = ai.config(3 if args.workload == "c3" else 2)
+    prob = ai.config(CONFIG_INDEX[args.workload])
     workload = prob.name
-    its_full = ORACLE_ITS["c3" if args.workload == "c3" else "c2"]
+    its_full = ORACLE_ITS[args.workload if args.workload in ORACLE_ITS else "c2"]
+    with_grad = args.workload == "c4"
     if args.workload == "c2block":
         prob = ai.sub_block(prob, tuple(int(v) for v in args.block.split(",")))
         workload = prob.name
     sample_desc = (f"ESTIMATE, not a complete run: oracle set-up of 4 of {prob.n_subs(1)} level-1 substructures "
                    f"(2x2x1 block at the clamped face) + one Algorithm-1 application, scaled by "
-                   f"{prob.n_subs(1) / 4:g} and by {its_full} PCG iterations")
+                   f"{prob.n_subs(1) / 4:g} and by {its_full} PCG iterations"
+                   + ("; the compliance gradient (one element loop) is not in it" if args.workload == "c4" else ""))
 
     if args.impl == "reference":
         if rank != 0:
@@ -277,9 +282,13 @@ def main():
     u_d = torch.empty_like(f_d)
     opts = dict(precision=prec, lobpcg_maxit=200, lobpcg_tol=1e-6, pcg_rtol=1e-8)
 
+    g_d = torch.empty(prob.n_el, dtype=torch.float64, device="cuda") if with_grad else None
+
     def step(timing=0):
         c = B.Context.from_problem(prob, coeff=coeff_d, timing_events=timing, **opts)
         _, info = c.solve(f_d, out=u_d)
+        if with_grad:
+            c.grad(B.QOI_COMPLIANCE, out=g_d)
         return c, info
 
     def barrier():
@@ -318,16 +327,19 @@ def main():
     # end to end: host coefficients / rhs / solution, copies inside the timed region
     coeff_h = np.ascontiguousarray(prob.coeff)
     u_h = np.empty_like(f_h)
+    g_h = np.empty(prob.n_el) if with_grad else None
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         c = B.Context.from_problem(prob, coeff=coeff_h, **opts)
         c.solve(f_h, out=u_h)
+        if with_grad:
+            c.grad(B.QOI_COMPLIANCE, out=g_h)
         c.close()
     barrier()
     e2e_s = (time.perf_counter() - t0) / args.steps
     h2d = coeff_h.nbytes + f_h.nbytes + prob.dirichlet_node_mask.nbytes + prob.elem_to_sub.nbytes
-    d2h = u_h.nbytes
+    d2h = u_h.nbytes + (g_h.nbytes if with_grad else 0)
 
     # kernel-family timing (separate, untimed run with CUDA events per family)
     c, info = step(timing=1)
@@ -510,6 +522,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == B.FP32 else "f64",
                 "data": "synthetic",
                 "config": {"workload": workload, "levels": prob.levels, "tau": prob.tau, "dofs": int(li.n_dofs),
+                           **({"step": "set-up + solve + compliance gradient"} if with_grad else {}),
                            "substructures": li.n_subs, "pairs": li.n_pairs, "l2": "working set >> L2 (no flush)",
                            "replicas": "one independent problem per GPU"},
                 "pcg_iterations": last.iterations, "rel_residual": last.rel_residual,
