@@ -32,7 +32,9 @@
  *    FP64 form eight FP32 digit slices per operand entry, 3.4 GB for the
  *    48^3 workload's largest update).  They grow to the largest need seen,
  *    are reused by later calls of the same thread and freed when the thread
- *    ends.  The set-up's host combinatorics run on up to 16 threads of
+ *    ends.  They live on the first GPU the thread works on: a thread that
+ *    later serves a context on another GPU gets AMB_EINVAL (serve each GPU's
+ *    contexts from threads of their own).  The set-up's host combinatorics run on up to 16 threads of
  *    their own, which end before the call returns; the environment variable
  *    AMB_HOST_THREADS (read once) caps them (1: the calling thread only).
  *    Their results do not depend on the number of threads.

@@ -205,20 +205,13 @@ int amb_setup(amb_ctx** out, const amb_mesh* mesh, const amb_coeffs* coeffs, con
     c->cfg.levels = levels;
     c->cfg.tau = tau;
     alloc_vectors(c);
-    cudaEvent_t e0, e1;
-    AMB_CUDA(cudaEventCreate(&e0));
-    AMB_CUDA(cudaEventCreate(&e1));
-    AMB_CUDA(cudaEventRecord(e0, c->st));
+    EventPair ev;
+    ev.start(c->st);
     c->eng = make_engine(opt->precision, m, c->cfg, c->st, c->ring, c->tm, c->reports, c->omega, c->nadapt, c->status);
     c->eng->setup();
-    AMB_CUDA(cudaEventRecord(e1, c->st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
+    const float ms = ev.lap(c->st);
     c->tm.phase_ms[7] += ms;
     c->setup_ms = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
   });
 }
 
@@ -228,10 +221,8 @@ int amb_solve(amb_ctx* c, const double* rhs, double* u, amb_solve_info* info) {
     AMB_CHECK(c->eng, AMB_EINVAL, "context has no successful set-up");
     AMB_CHECK(rhs && u, AMB_EINVAL, "NULL vector");
     const int64_t n = c->mesh.ndof;
-    cudaEvent_t e0, e1;
-    AMB_CUDA(cudaEventCreate(&e0));
-    AMB_CUDA(cudaEventCreate(&e1));
-    AMB_CUDA(cudaEventRecord(e0, c->st));
+    EventPair ev;
+    ev.start(c->st);
     copy_in(c->f, rhs, n * sizeof(double), c->st);
     double rel = 0, cond = 1;
     const int its = pcg(c, &rel, &cond);
@@ -243,12 +234,7 @@ int amb_solve(amb_ctx* c, const double* rhs, double* u, amb_solve_info* info) {
     const double nf = std::sqrt(dotd(c, dptr<double>(c->f), dptr<double>(c->f), n));
     const double nr = std::sqrt(dotd(c, dptr<double>(c->tmp), dptr<double>(c->tmp), n));
     copy_out(u, c->u.p, n * sizeof(double), c->st);
-    AMB_CUDA(cudaEventRecord(e1, c->st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    const float ms = ev.lap(c->st);
     c->tm.phase_ms[5] += ms;
     c->last_its = its;
     c->last_cond = cond;
@@ -333,10 +319,8 @@ int amb_grad(amb_ctx* c, int32_t qoi_kind, const double* dq_du, double* grad) {
     AMB_CHECK(grad, AMB_EINVAL, "NULL gradient buffer");
     const Mesh& m = c->mesh;
     const int64_t n = m.ndof;
-    cudaEvent_t e0, e1;
-    AMB_CUDA(cudaEventCreate(&e0));
-    AMB_CUDA(cudaEventCreate(&e1));
-    AMB_CUDA(cudaEventRecord(e0, c->st));
+    EventPair ev;
+    ev.start(c->st);
     // keep the primal solution: lam buffer receives u, adjoint overwrites u/f
     AMB_CUDA(cudaMemcpyAsync(c->lam.p, c->u.p, n * sizeof(double), cudaMemcpyDeviceToDevice, c->st));
     const double* lam = dptr<double>(c->lam);
@@ -360,13 +344,7 @@ int amb_grad(amb_ctx* c, int32_t qoi_kind, const double* dq_du, double* grad) {
     element_gradient(c->st, dptr<double>(c->grad), dptr<double>(c->u), lam, dptr<double>(m.coeff), dptr<double>(m.khat),
                      dptr<uint8_t>(m.dir), m.nx, m.ny, m.nz, m.dpn);
     copy_out(grad, c->grad.p, m.nel * sizeof(double), c->st);
-    AMB_CUDA(cudaEventRecord(e1, c->st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    c->tm.phase_ms[6] += ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    c->tm.phase_ms[6] += ev.lap(c->st);
   });
 }
 
@@ -463,7 +441,9 @@ int amb_plan(const amb_mesh* mesh, const amb_partition* part, int32_t levels, in
     return AMB_OK;
   } catch (const Error& e) {
     return e.status;
-  } catch (const std::exception&) {
+  } catch (const std::bad_alloc&) {
+    return AMB_ENOMEM;
+  } catch (...) {
     return AMB_EINVAL;
   }
 }

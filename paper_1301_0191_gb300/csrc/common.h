@@ -89,6 +89,20 @@ struct DevBuf {
 template <typename T>
 inline T* dptr(const DevBuf& b) { return static_cast<T*>(b.p); }
 
+// A host thread's device workspaces (operand slabs of the tensor-core
+// products, scratch of the diagonal blocks: grown on demand and kept for the
+// thread's life) are allocated on the first device the thread works on.
+// A later call of the same thread on another device is refused here rather
+// than handing that device a pointer into another GPU's memory.
+inline void check_workspace_device() {
+  static thread_local int dev = -1;
+  int d = 0;
+  AMB_CUDA(cudaGetDevice(&d));
+  if (dev < 0) dev = d;
+  AMB_CHECK(d == dev, AMB_EINVAL,
+            "this host thread holds device workspaces on another GPU: serve each GPU's contexts from its own threads");
+}
+
 template <typename T>
 inline void upload(DevBuf& b, const std::vector<T>& v, cudaStream_t st) {
   b.alloc(v.size() * sizeof(T));

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <memory>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -57,8 +58,18 @@ int guarded(amb_ctx* c, F&& fn) {
     c->err = e.what();
     c->launches_total += g_launches - l0;
     return e.status;
+  } catch (const std::bad_alloc& e) {
+    c->err = std::string("host allocation failed: ") + e.what();
+    c->launches_total += g_launches - l0;
+    return AMB_ENOMEM;
   } catch (const std::exception& e) {
     c->err = e.what();
+    c->launches_total += g_launches - l0;
+    return AMB_EINVAL;
+  } catch (...) {
+    // nothing may cross the C boundary
+    c->err = "unknown exception";
+    c->launches_total += g_launches - l0;
     return AMB_EINVAL;
   }
 }

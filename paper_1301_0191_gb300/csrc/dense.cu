@@ -909,6 +909,7 @@ __global__ void __launch_bounds__(256) k_chol_diag(const DiagDesc* descs, T* bas
 // scratch space for the diagonal inverses, grown on demand
 template <typename T>
 static T* diag_scratch(size_t nblocks) {
+  check_workspace_device();
   static thread_local DevBuf buf;
   size_t need = nblocks * kNB * kNB * sizeof(T);
   if (buf.bytes < need) {

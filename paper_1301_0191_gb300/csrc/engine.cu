@@ -459,10 +459,8 @@ void Engine<T>::setup() {
     auto L = std::make_unique<LevelData<T>>();
     L->level = i + 1;
     std::vector<int32_t> loc;
-    cudaEvent_t e0, e1;
-    AMB_CUDA(cudaEventCreate(&e0));
-    AMB_CUDA(cudaEventCreate(&e1));
-    AMB_CUDA(cudaEventRecord(e0, st));
+    EventPair ev;
+    ev.start(st);
     if (i == 0) {
       std::vector<int32_t> elem_local;
       L->topo = build_level_one(mesh.nx, mesh.ny, mesh.nz, mesh.dpn, mesh.dir_h.data(), mesh.elem_sub_h.data(),
@@ -473,42 +471,24 @@ void Engine<T>::setup() {
     }
     alloc_level(*L);
     assemble(*L, prev, loc);
-    AMB_CUDA(cudaEventRecord(e1, st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    float ms = 0;
-    cudaEventElapsedTime(&ms, e0, e1);
-    tm.phase_ms[0] += ms;
-    AMB_CUDA(cudaEventRecord(e0, st));
+    tm.phase_ms[0] += ev.lap(st);
+    ev.start(st);
     factor_level(*L);
-    AMB_CUDA(cudaEventRecord(e1, st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    cudaEventElapsedTime(&ms, e0, e1);
-    tm.phase_ms[1] += ms;
-    AMB_CUDA(cudaEventRecord(e0, st));
+    tm.phase_ms[1] += ev.lap(st);
+    ev.start(st);
     coarse_basis(*L);
-    AMB_CUDA(cudaEventRecord(e1, st));
-    AMB_CUDA(cudaEventSynchronize(e1));
-    cudaEventElapsedTime(&ms, e0, e1);
-    tm.phase_ms[4] += ms;
+    tm.phase_ms[4] += ev.lap(st);
     if (cfg.opt.adaptive) {
-      AMB_CUDA(cudaEventRecord(e0, st));
+      ev.start(st);
       adapt_level(*L);
-      AMB_CUDA(cudaEventRecord(e1, st));
-      AMB_CUDA(cudaEventSynchronize(e1));
-      cudaEventElapsedTime(&ms, e0, e1);
-      tm.phase_ms[2] += ms;
-      AMB_CUDA(cudaEventRecord(e0, st));
+      tm.phase_ms[2] += ev.lap(st);
+      ev.start(st);
       coarse_basis(*L);
-      AMB_CUDA(cudaEventRecord(e1, st));
-      AMB_CUDA(cudaEventSynchronize(e1));
-      cudaEventElapsedTime(&ms, e0, e1);
-      tm.phase_ms[4] += ms;
+      tm.phase_ms[4] += ev.lap(st);
     } else {
       omega.push_back(0.0);
       nadapt.push_back(0);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     lv.push_back(std::move(L));
     prev = lv.back().get();
   }

@@ -823,6 +823,7 @@ CUtensorMap slab_map(float* base, int64_t rows, int kp, int box_rows = kTM) {
 
 // workspace slab for the split operands, grown on demand
 float* tc_slab(size_t floats) {
+  check_workspace_device();
   static thread_local DevBuf buf;
   const size_t need = 2 * floats * sizeof(float);
   if (buf.bytes < need) {
@@ -942,6 +943,7 @@ void run_oz(cudaStream_t st, DescRing& ring, const std::vector<TcSplitDesc>& sp,
     AMB_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmemBytes));
     attr = true;
   }
+  check_workspace_device();
   static thread_local DevBuf slab_buf, ex_buf;
   const size_t need = (size_t)kOzSlices * rows * kp * sizeof(float);
   if (slab_buf.bytes < need || ex_buf.bytes < (size_t)rows * sizeof(int)) {

@@ -14,6 +14,33 @@ struct Timers {
   double fam_bytes[AMB_FAM_N] = {0};
 };
 
+// Two events that time a section of work on one stream, destroyed on every
+// exit path (an error thrown inside the section included).  start() records
+// the first, lap() records the second, waits for it and returns the elapsed
+// milliseconds; lap() may be followed by start() for the next section.
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+  void start(cudaStream_t st) {
+    if (!a) AMB_CUDA(cudaEventCreate(&a));
+    if (!b) AMB_CUDA(cudaEventCreate(&b));
+    AMB_CUDA(cudaEventRecord(a, st));
+  }
+  float lap(cudaStream_t st) {
+    AMB_CUDA(cudaEventRecord(b, st));
+    AMB_CUDA(cudaEventSynchronize(b));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+};
+
 // Event pair around a kernel family section (only when timing is enabled).
 struct FamTimer {
   cudaStream_t st;
