@@ -1,16 +1,22 @@
 """bench.py's reference arm (the CPU oracle on a bounded sample of the 48^3
-workload) prints one JSON line with the contract's keys; it needs no GPU."""
+workload, or of the 64^3 gradient workload) prints one JSON line with the
+contract's keys; it needs no GPU."""
 import json
 import os
 import subprocess
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_reference_arm_prints_one_contract_line():
+@pytest.mark.parametrize("workload,name", [(None, "elasticity48_4x4x4_lognormal"),
+                                           ("c4", "poisson64_4x4x4_grf")])
+def test_reference_arm_prints_one_contract_line(workload, name):
+    extra = ["--workload", workload] if workload else []
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+                        "--warmup", "0"] + extra, capture_output=True, text=True, timeout=600, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
     assert len(lines) == 1
@@ -22,4 +28,4 @@ def test_reference_arm_prints_one_contract_line():
     assert d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["config"]["workload"] == "elasticity48_4x4x4_lognormal"
+    assert d["config"]["workload"] == name
